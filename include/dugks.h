@@ -1,0 +1,143 @@
+/*
+ * dugks.h -- C ABI of libdugks.so: the discrete unified gas-kinetic scheme
+ * (DUGKS) time step for the conservative Allen-Cahn equation on a uniform,
+ * periodic 2D D2Q9 grid, on one GB300 GPU (sm_103a).
+ *
+ * Method: Yang, Zhong & Zhuo, "Performance evaluation of high-order
+ * reconstruction for discrete unified gas-kinetic scheme in tracking fluid
+ * interfaces". Equation numbers below are the paper's.
+ *
+ * Conventions shared by every call:
+ *  - Cells are unit squares (Sec. III: "cell size of unity"); cell (i, j) has its
+ *    centre at (i + 1/2, j + 1/2); host arrays are row-major, x fastest, ny * nx.
+ *  - D2Q9 velocities xi_k = e_k in the order (0,0),(1,0),(1,1),(0,1),(-1,1),
+ *    (-1,0),(-1,-1),(0,-1),(1,-1); RT = 1/3; tau = M / RT; dt = cfl (Eq. (39)).
+ *  - Every call returns a dugks_status_code. Errors of asynchronous device work are
+ *    sticky: they are recorded in the context and returned by the next call
+ *    that synchronises (dugks_read_phi, dugks_mass, dugks_save_state,
+ *    dugks_status). After an error, dugks_last_error() describes it.
+ *  - A context owns all of its device memory; every host pointer stays owned by
+ *    the caller and is only read or written during the call. A context is used
+ *    by one host thread at a time.
+ *  - Nothing falls back to the CPU: without a usable CUDA device, dugks_create
+ *    returns DUGKS_ECUDA.
+ */
+#ifndef DUGKS_H
+#define DUGKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dugks_ctx dugks_ctx;
+
+typedef enum {
+    DUGKS_OK = 0,
+    DUGKS_EINVAL = 1,      /* bad argument or parameter set */
+    DUGKS_ENOMEM = 2,      /* device allocation failed */
+    DUGKS_ECUDA = 3,       /* CUDA runtime error (message in dugks_last_error) */
+    DUGKS_ETIMEOUT = 4,    /* a bounded device wait ran out */
+    DUGKS_ENONFINITE = 5,  /* the field holds NaN or Inf */
+    DUGKS_ESTATE = 6       /* call not valid in the context's current state */
+} dugks_status_code;
+
+enum { DUGKS_FP64 = 0, DUGKS_FP32 = 1, DUGKS_FP16F = 2 };
+enum { DUGKS_UPWIND = 0, DUGKS_CENTRAL = 1 };
+enum { DUGKS_VEL_UNIFORM = 0, DUGKS_VEL_ROTATION = 1, DUGKS_VEL_VORTEX = 2, DUGKS_VEL_FIELD = 3 };
+
+/* Problem statement (Sec. II-III): interface width W, mobility M, CFL number,
+ * isotropic stencil order, face reconstruction, number of stages.
+ *   nx, ny     cells, each >= 8.
+ *   W > 0      interface width in cells (Eq. (3), (4)).
+ *   M > 0      mobility of Eq. (1); tau = 3 M.
+ *   cfl        in (0, 1]; dt = cfl.
+ *   order      2, 3 or 4: derivative stencils and Taylor degree order - 1 of the
+ *              upwind reconstruction Eq. (26); gradient order of Eq. (2).
+ *   flux       DUGKS_UPWIND (Eq. (26)) or DUGKS_CENTRAL (Eq. (25)).
+ *   stages     2: original two-stage DUGKS; 3: three-stage third-order DUGKS
+ *              (Sec. II.B.2), which needs dt < 12 tau (Sec. III.A).
+ *   precision  DUGKS_FP64, DUGKS_FP32, or DUGKS_FP16F (FP32 arithmetic; f stored
+ *              in half precision as the scaled deviation f_k - w_k phi, phi kept
+ *              in FP32; two-stage only).
+ *   dtphiu     1 keeps the d(phi u)/dt term of the source Eq. (14b), evaluated
+ *              by a backward difference over the last step; 0 drops it.
+ *   phiA, phiB phase indicators (Eq. (3)), phiA != phiB; usually 1 and 0. */
+typedef struct {
+    int32_t nx, ny;
+    double W, M, cfl;
+    int32_t order, flux, stages, precision, dtphiu;
+    double phiA, phiB;
+} dugks_params;
+
+/* Validates p, allocates the state on the current CUDA device and uploads phi0
+ * (ny * nx doubles, host). cuda_stream is a cudaStream_t the context launches
+ * on; NULL makes the context create and own a stream. The initial distribution
+ * (f = f^eq, Omega = 0) is built on the device at the first dugks_step /
+ * read / save after the velocity is set (default: uniform zero velocity).
+ * Returns DUGKS_EINVAL (bad p, also stages == 3 with dt >= 12 tau, or FP16F
+ * with stages == 3), DUGKS_ENOMEM or DUGKS_ECUDA; *out is NULL on error. */
+int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stream, dugks_ctx **out);
+
+/* Sets the prescribed divergence-free velocity (Sec. II.A).
+ *   UNIFORM  params = (ux, uy)
+ *   ROTATION params = (cx, cy, omega): u = -omega (y - cy), v = omega (x - cx)
+ *   VORTEX   params = (L, U, T): u = -U sin^2(pi x/L) sin(2 pi y/L) cos(pi t/T),
+ *                                v =  U sin^2(pi y/L) sin(2 pi x/L) cos(pi t/T)
+ *   FIELD    u_host, v_host = ny * nx cell-centre components (copied); a face
+ *            takes the mean of its two cells.
+ * Analytic fields are evaluated in the kernels at each point and time.
+ * Allowed before the first step (it then defines the initial equilibrium) or
+ * later (the new field applies from the next step). */
+int dugks_set_velocity(dugks_ctx *c, int kind, const double *params, const double *u_host,
+                       const double *v_host);
+
+/* Enqueues nsteps >= 0 full time steps on the context's stream and returns
+ * without waiting. Two-stage: one fused kernel per step (stages a1-a5 of the
+ * method: cell moments and bar f^+ with source, isotropic gradients, face
+ * reconstruction at x_b - xi h, face phi / f^eq / source / original f,
+ * meso-flux update), which also writes per-tile FP64 mass partials.
+ * Three-stage: two kernels per step (steps (i)-(ii) and (iii)-(iv)). */
+int dugks_step(dugks_ctx *c, int64_t nsteps);
+
+/* Waits for the stream and writes phi = sum_k f_k (Eq. (30)) into out_host
+ * (ny * nx doubles). */
+int dugks_read_phi(dugks_ctx *c, double *out_host);
+
+/* Enqueues phi into a device buffer dev_out of ny * nx elements of the
+ * context's arithmetic type (double for FP64, float otherwise); no wait. */
+int dugks_read_phi_device(dugks_ctx *c, void *dev_out);
+
+/* Waits and returns the total mass sum phi over all cells, reduced in FP64 in
+ * a fixed order (deterministic). DUGKS_ENONFINITE if it is NaN or Inf. */
+int dugks_mass(dugks_ctx *c, double *out);
+
+/* Enqueues the same reduction into dev_out (one double, device); no wait. */
+int dugks_mass_device(dugks_ctx *c, double *dev_out);
+
+/* Waits for the stream and returns the sticky status. */
+int dugks_status(dugks_ctx *c);
+
+/* Text of the last error; never NULL (empty when there was none). */
+const char *dugks_last_error(const dugks_ctx *c);
+
+/* Number of steps taken since creation (or as restored by dugks_load_state). */
+int64_t dugks_step_index(const dugks_ctx *c);
+
+/* Checkpoint: raw device state (distribution planes, phi planes) in the
+ * context's storage layout. dugks_state_bytes gives the size. save waits and
+ * copies to host; load copies from host and sets the step index. The bytes
+ * are only meaningful to a context created with the same dugks_params. */
+size_t dugks_state_bytes(const dugks_ctx *c);
+int dugks_save_state(dugks_ctx *c, void *host, size_t bytes, int64_t *step_index);
+int dugks_load_state(dugks_ctx *c, const void *host, size_t bytes, int64_t step_index);
+
+/* Frees everything; NULL-safe; waits for the context's outstanding work. */
+void dugks_destroy(dugks_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

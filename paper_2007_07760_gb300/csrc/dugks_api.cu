@@ -1,0 +1,596 @@
+// dugks_api.cu -- the C ABI of libdugks.so (declared in include/dugks.h).
+//
+// Host logic only: parameter checks, device memory of a context, the
+// per-step coefficients of the method, buffer rotation and error handling.
+// All arithmetic of the time step runs in the kernels of dugks_kernels.cuh.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/dugks.h"
+#include "dugks_internal.h"
+
+using namespace dugks;
+
+struct dugks_ctx {
+    dugks_params p{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int pitch = 0;
+    size_t plane = 0;           // ny * pitch elements
+    size_t tsize = 8, ssize = 8;
+    int nsets = 2, nphi = 2;
+    void *X[3] = {nullptr, nullptr, nullptr};
+    void *phi[3] = {nullptr, nullptr, nullptr};
+    int cur = 0;                // current state set (two-stage)
+    int pr[3] = {0, 1, 2};      // phi plane roles (see step_*)
+    void *phi0 = nullptr;       // initial phi (T)
+    void *ufield = nullptr, *vfield = nullptr;
+    void *tmp = nullptr;        // ny * nx T, phi readout
+    double *partial = nullptr;  // per-tile FP64 mass partials (scratch)
+    double *dmass = nullptr;    // one double
+    int *dstatus = nullptr;     // sticky device flags
+    int ntiles = 0, tiles_x = 0;
+    int vel_kind = DUGKS_VEL_UNIFORM;
+    double vel[4] = {0, 0, 0, 0};
+    bool initialized = false;
+    bool mass_valid = false;
+    int64_t step = 0;
+    int sticky = DUGKS_OK;
+    std::string err;
+};
+
+namespace {
+
+int fail(dugks_ctx *c, int code, const std::string &msg) {
+    if (c) {
+        if (c->sticky == DUGKS_OK) c->sticky = code;
+        c->err = msg;
+    }
+    return code;
+}
+
+int cuda_fail(dugks_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, DUGKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_fp64(const dugks_ctx *c) { return c->p.precision == DUGKS_FP64; }
+
+int check_params(const dugks_params *p, std::string &why) {
+    if (!p) { why = "params is NULL"; return DUGKS_EINVAL; }
+    if (p->nx < 8 || p->ny < 8) { why = "nx and ny must be >= 8"; return DUGKS_EINVAL; }
+    if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) { why = "grid too large"; return DUGKS_EINVAL; }
+    if (!(p->W > 0) || !(p->M > 0)) { why = "W and M must be > 0"; return DUGKS_EINVAL; }
+    if (!(p->cfl > 0) || p->cfl > 1.0) { why = "cfl must be in (0, 1]"; return DUGKS_EINVAL; }
+    if (p->order < 2 || p->order > 4) { why = "order must be 2, 3 or 4"; return DUGKS_EINVAL; }
+    if (p->flux != DUGKS_UPWIND && p->flux != DUGKS_CENTRAL) { why = "flux must be upwind or central"; return DUGKS_EINVAL; }
+    if (p->stages != 2 && p->stages != 3) { why = "stages must be 2 or 3"; return DUGKS_EINVAL; }
+    if (p->precision < DUGKS_FP64 || p->precision > DUGKS_FP16F) { why = "unknown precision"; return DUGKS_EINVAL; }
+    if (p->precision == DUGKS_FP16F && p->stages != 2) { why = "FP16 storage is two-stage only"; return DUGKS_EINVAL; }
+    if (!(p->phiA != p->phiB) || !std::isfinite(p->phiA) || !std::isfinite(p->phiB)) { why = "phiA must differ from phiB"; return DUGKS_EINVAL; }
+    if (p->stages == 3 && !(p->cfl < 12.0 * 3.0 * p->M)) {
+        why = "three-stage DUGKS needs dt < 12 tau = 36 M";
+        return DUGKS_EINVAL;
+    }
+    return DUGKS_OK;
+}
+
+template <typename T>
+StepParams<T> base_params(const dugks_ctx *c) {
+    StepParams<T> q;
+    std::memset(&q, 0, sizeof q);
+    q.nx = c->p.nx;
+    q.ny = c->p.ny;
+    q.pitch = c->pitch;
+    q.tiles_x = c->tiles_x;
+    q.ufield = static_cast<const T *>(c->ufield);
+    q.vfield = static_cast<const T *>(c->vfield);
+    const double tau = 3.0 * c->p.M;
+    q.tau = (T)tau;
+    q.theta_c = (T)(-4.0 / (c->p.W * (c->p.phiA - c->p.phiB)));
+    q.phiA = (T)c->p.phiA;
+    q.phiB = (T)c->p.phiB;
+    q.vel_kind = c->vel_kind;
+    q.vp0 = (T)c->vel[0];
+    q.vp1 = (T)c->vel[1];
+    q.vp2 = (T)c->vel[2];
+    q.qscale = (T)256.0;
+    q.qinv = (T)(1.0 / 256.0);
+    return q;
+}
+
+// f_b = (2 tau bar f + h f^eq + tau h S) / (2 tau + h)        (Eq. (27))
+template <typename T>
+void face_coefs(StepParams<T> &q, double tau, double h) {
+    q.h = (T)h;
+    q.c1 = (T)(2.0 * tau / (2.0 * tau + h));
+    q.c2 = (T)(h / (2.0 * tau + h));
+    q.c3 = (T)(tau * h / (2.0 * tau + h));
+}
+
+template <typename T, typename ST>
+int run_init(dugks_ctx *c) {
+    StepParams<T> q = base_params<T>(c);
+    q.t = (T)0;
+    const double frac = c->p.stages == 2 ? 0.5 : 0.25;
+    if (Store<T, ST>::deviation) {
+        c->pr[0] = 0; c->pr[1] = 1; c->pr[2] = 2;
+        q.out1 = c->X[c->cur];
+        q.phi_out = static_cast<T *>(c->phi[c->pr[0]]);
+    } else {
+        q.out1 = c->X[c->cur];
+    }
+    cudaError_t e = Launch<T, ST>::init(q, static_cast<const T *>(c->phi0), (T)(frac * c->p.cfl), c->p.order, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
+    if (!Store<T, ST>::deviation) {
+        // previous phi for d(phi u)/dt: phi0 (unused at the first step, where D = 0)
+        e = cudaMemcpyAsync(c->phi[c->pr[0]], c->phi0, c->plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "init copy");
+    }
+    c->initialized = true;
+    c->mass_valid = false;
+    return DUGKS_OK;
+}
+
+int ensure_init(dugks_ctx *c) {
+    if (c->initialized) return DUGKS_OK;
+    switch (c->p.precision) {
+    case DUGKS_FP64: return run_init<double, double>(c);
+    case DUGKS_FP32: return run_init<float, float>(c);
+    default: return run_init<float, __half>(c);
+    }
+}
+
+// One two-stage step.  Non-deviation storage: X[cur] -> X[1-cur]; phi[pr0]
+// holds phi^{n-1} and receives nothing, phi[pr1] receives phi^n.
+// Deviation storage: phi[pr0] = phi^n (of X), phi[pr1] = phi^{n-1},
+// phi[pr2] receives phi^{n+1}.
+template <typename T, typename ST>
+int step_t2(dugks_ctx *c) {
+    StepParams<T> q = base_params<T>(c);
+    const double dt = c->p.cfl, tau = 3.0 * c->p.M, h = 0.5 * dt;
+    const double a = (2.0 * tau - h) / (2.0 * tau + dt), b = (dt + h) / (2.0 * tau + dt);
+    const double t = (double)c->step * dt;
+    q.a = (T)a;
+    q.b = (T)b;
+    face_coefs(q, tau, h);
+    // tilde f^{n+1} = (4/3) bar f^+ - (1/3) tilde f + dt L
+    q.al1 = (T)(4.0 / 3.0 * a - 1.0 / 3.0);
+    q.be1 = (T)(4.0 / 3.0 * b);
+    q.ga1 = (T)dt;
+    q.t = (T)t;
+    q.t_old = (T)(t - dt);
+    q.t_face = (T)(t + h);
+    q.useD = (c->p.dtphiu && c->step > 0) ? 1 : 0;
+    q.inv_dtD = (T)(1.0 / dt);
+    q.X = c->X[c->cur];
+    q.out1 = c->X[1 - c->cur];
+    q.mass_partial = c->partial;
+    if (Store<T, ST>::deviation) {
+        q.phi_cur = static_cast<const T *>(c->phi[c->pr[0]]);
+        q.phi_old = static_cast<const T *>(c->phi[c->pr[1]]);
+        q.phi_out = static_cast<T *>(c->phi[c->pr[2]]);
+    } else {
+        q.phi_old = static_cast<const T *>(c->phi[c->pr[0]]);
+        q.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
+    }
+    cudaError_t e = Launch<T, ST>::step(q, c->p.order, c->p.flux, KIND_T2, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
+    c->cur = 1 - c->cur;
+    if (Store<T, ST>::deviation) {
+        const int a0 = c->pr[0], a1 = c->pr[1], a2 = c->pr[2];
+        c->pr[0] = a2; c->pr[1] = a0; c->pr[2] = a1;
+    } else {
+        std::swap(c->pr[0], c->pr[1]);
+    }
+    return DUGKS_OK;
+}
+
+// One three-stage step (Sec. II.B.2): X[0] = hat f, X[1] = tilde f at t',
+// X[2] = accumulator f^n + (3 dt / 7) L*.
+template <typename T>
+int step_t3(dugks_ctx *c) {
+    const double dt = c->p.cfl, tau = 3.0 * c->p.M;
+    const double t = (double)c->step * dt;
+    // (i)-(ii): bar f^{+, dt/6} (Eq. (31)), flux at t_n + dt/6, tilde f(t') and accumulator
+    StepParams<T> A = base_params<T>(c);
+    const double a1 = (12.0 * tau - dt) / (12.0 * tau + 3.0 * dt), b1 = 4.0 * dt / (12.0 * tau + 3.0 * dt);
+    A.a = (T)a1;
+    A.b = (T)b1;
+    face_coefs(A, tau, dt / 6.0);
+    A.al1 = (T)(1.25 * a1 - 0.25);   // tilde f^+ = (5/4) A - (1/4) hat f   (Eq. (33))
+    A.be1 = (T)(1.25 * b1);
+    A.ga1 = (T)(dt / 3.0);           // Eq. (15)
+    A.al2 = (T)(0.75 * a1 + 0.25);   // f^n = (3/4) A + (1/4) hat f         (Eq. (32))
+    A.be2 = (T)(0.75 * b1);
+    A.ga2 = (T)(3.0 * dt / 7.0);     // Eq. (16)
+    A.t = (T)t;
+    A.t_old = (T)(t - dt);
+    A.t_face = (T)(t + dt / 6.0);
+    A.useD = (c->p.dtphiu && c->step > 0) ? 1 : 0;
+    A.inv_dtD = (T)(1.0 / dt);
+    A.X = c->X[0];
+    A.out1 = c->X[1];
+    A.out2 = static_cast<T *>(c->X[2]);
+    A.phi_old = static_cast<const T *>(c->phi[c->pr[0]]);
+    A.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
+    cudaError_t e = Launch<T, T>::step(A, c->p.order, c->p.flux, KIND_T3A, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "three-stage kernel A");
+    // (iii)-(iv): bar f^{+, 5dt/12}(t') (Eq. (34)), flux at t_n + 3dt/4, hat f^{n+1}
+    StepParams<T> B = base_params<T>(c);
+    const double a2 = (24.0 * tau - 5.0 * dt) / (24.0 * tau + 4.0 * dt), b2 = 9.0 * dt / (24.0 * tau + 4.0 * dt);
+    const double cos_ = -6.0 / (6.0 * tau + dt);   // Eq. (29), stray dt read as a typo
+    B.a = (T)a2;
+    B.b = (T)b2;
+    face_coefs(B, tau, 5.0 * dt / 12.0);
+    B.al1 = (T)(0.75 * dt * cos_);
+    B.be1 = (T)(-0.75 * dt * cos_);
+    B.ga1 = (T)(4.0 * dt / 7.0);
+    B.t = (T)(t + dt / 3.0);
+    B.t_old = (T)t;
+    B.t_face = (T)(t + 0.75 * dt);
+    B.useD = c->p.dtphiu ? 1 : 0;
+    B.inv_dtD = (T)(3.0 / dt);
+    B.X = c->X[1];
+    B.acc = c->X[2];
+    B.out1 = c->X[0];
+    B.phi_old = static_cast<const T *>(c->phi[c->pr[1]]);
+    B.mass_partial = c->partial;
+    e = Launch<T, T>::step(B, c->p.order, c->p.flux, KIND_T3B, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "three-stage kernel B");
+    std::swap(c->pr[0], c->pr[1]);
+    return DUGKS_OK;
+}
+
+int step_once(dugks_ctx *c) {
+    int r;
+    if (c->p.stages == 3) {
+        r = is_fp64(c) ? step_t3<double>(c) : step_t3<float>(c);
+    } else {
+        switch (c->p.precision) {
+        case DUGKS_FP64: r = step_t2<double, double>(c); break;
+        case DUGKS_FP32: r = step_t2<float, float>(c); break;
+        default: r = step_t2<float, __half>(c); break;
+        }
+    }
+    if (r == DUGKS_OK) {
+        c->step++;
+        c->mass_valid = true;
+    }
+    return r;
+}
+
+template <typename T, typename ST>
+StepParams<T> state_view(const dugks_ctx *c) {
+    StepParams<T> q = base_params<T>(c);
+    q.X = c->p.stages == 3 ? c->X[0] : c->X[c->cur];
+    if (Store<T, ST>::deviation) q.phi_cur = static_cast<const T *>(c->phi[c->pr[0]]);
+    q.mass_partial = c->partial;
+    return q;
+}
+
+int enqueue_mass(dugks_ctx *c, double *dev_out) {
+    cudaError_t e;
+    if (!c->mass_valid) {
+        switch (c->p.precision) {
+        case DUGKS_FP64: e = Launch<double, double>::mass_partial(state_view<double, double>(c), c->stream); break;
+        case DUGKS_FP32: e = Launch<float, float>::mass_partial(state_view<float, float>(c), c->stream); break;
+        default: e = Launch<float, __half>::mass_partial(state_view<float, __half>(c), c->stream); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "mass partial kernel");
+        c->mass_valid = true;
+    }
+    e = launch_mass_final(c->partial, c->ntiles, dev_out, c->dstatus, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mass kernel");
+    return DUGKS_OK;
+}
+
+int enqueue_phi(dugks_ctx *c, void *dev_out) {
+    cudaError_t e;
+    switch (c->p.precision) {
+    case DUGKS_FP64: e = Launch<double, double>::phi(state_view<double, double>(c), static_cast<double *>(dev_out), c->stream); break;
+    case DUGKS_FP32: e = Launch<float, float>::phi(state_view<float, float>(c), static_cast<float *>(dev_out), c->stream); break;
+    default: e = Launch<float, __half>::phi(state_view<float, __half>(c), static_cast<float *>(dev_out), c->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "phi kernel");
+    return DUGKS_OK;
+}
+
+int sync_ctx(dugks_ctx *c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    return c->sticky;
+}
+
+void free_ctx(dugks_ctx *c) {
+    for (void *q : {c->X[0], c->X[1], c->X[2], c->phi[0], c->phi[1], c->phi[2], c->phi0, c->ufield,
+                    c->vfield, c->tmp, (void *)c->partial, (void *)c->dmass, (void *)c->dstatus})
+        if (q) cudaFree(q);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+// host doubles (ny * nx) -> device T plane with pitch
+int upload_plane(dugks_ctx *c, void *dst, const double *src) {
+    const int nx = c->p.nx, ny = c->p.ny;
+    cudaError_t e;
+    if (is_fp64(c)) {
+        e = cudaMemcpy2DAsync(dst, c->pitch * sizeof(double), src, nx * sizeof(double), nx * sizeof(double), ny,
+                              cudaMemcpyHostToDevice, c->stream);
+    } else {
+        std::vector<float> tmp((size_t)nx * ny);
+        for (size_t i = 0; i < tmp.size(); i++) tmp[i] = (float)src[i];
+        e = cudaMemcpy2DAsync(dst, c->pitch * sizeof(float), tmp.data(), nx * sizeof(float), nx * sizeof(float), ny,
+                              cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // tmp goes out of scope
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+    return DUGKS_OK;
+}
+
+}  // namespace
+
+namespace dugks {
+// Fixed-order sum of the per-tile partials (deterministic); flags NaN / Inf.
+__global__ void __launch_bounds__(256) mass_final_kernel(const double *partial, int n, double *out, int *status) {
+    __shared__ double sred[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    s = block_sum(s, sred);
+    if (threadIdx.x == 0) {
+        *out = s;
+        if (!isfinite(s)) atomicOr(status, 1);
+    }
+}
+
+cudaError_t launch_mass_final(const double *partial, int n, double *out, int *status, cudaStream_t s) {
+    mass_final_kernel<<<1, 256, 0, s>>>(partial, n, out, status);
+    return cudaGetLastError();
+}
+}  // namespace dugks
+
+extern "C" {
+
+int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stream, dugks_ctx **out) {
+    if (!out) return DUGKS_EINVAL;
+    *out = nullptr;
+    std::string why;
+    int r = check_params(p, why);
+    if (r != DUGKS_OK) return r;
+    if (!phi0_host) return DUGKS_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DUGKS_ECUDA;
+    dugks_ctx *c = new dugks_ctx();
+    c->p = *p;
+    cudaGetDevice(&c->dev);
+    if (cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            free_ctx(c);
+            return DUGKS_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    c->tsize = is_fp64(c) ? 8 : 4;
+    c->ssize = p->precision == DUGKS_FP64 ? 8 : p->precision == DUGKS_FP32 ? 4 : 2;
+    c->pitch = (p->nx + 31) / 32 * 32;
+    c->plane = (size_t)p->ny * c->pitch;
+    c->nsets = p->stages == 3 ? 3 : 2;
+    c->nphi = p->precision == DUGKS_FP16F ? 3 : 2;
+    c->tiles_x = (p->nx + TILE_X - 1) / TILE_X;
+    c->ntiles = c->tiles_x * ((p->ny + TILE_Y - 1) / TILE_Y);
+    bool ok = true;
+    for (int s = 0; s < c->nsets && ok; s++) {
+        // the three-stage accumulator (set 2) is always in the arithmetic type
+        size_t es = (p->stages == 3) ? c->tsize : c->ssize;
+        ok = cudaMalloc(&c->X[s], 9 * c->plane * es) == cudaSuccess;
+    }
+    for (int s = 0; s < c->nphi && ok; s++) ok = cudaMalloc(&c->phi[s], c->plane * c->tsize) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->phi0, c->plane * c->tsize) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->tmp, (size_t)p->nx * p->ny * c->tsize) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->partial, (size_t)c->ntiles * sizeof(double)) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->dmass, sizeof(double)) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_ctx(c);
+        return DUGKS_ENOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
+    // zero the pitch padding so raw checkpoints are deterministic
+    for (int s = 0; s < c->nsets && e == cudaSuccess; s++)
+        e = cudaMemsetAsync(c->X[s], 0, 9 * c->plane * ((p->stages == 3) ? c->tsize : c->ssize), c->stream);
+    for (int s = 0; s < c->nphi && e == cudaSuccess; s++) e = cudaMemsetAsync(c->phi[s], 0, c->plane * c->tsize, c->stream);
+    if (e != cudaSuccess) {
+        free_ctx(c);
+        return DUGKS_ECUDA;
+    }
+    for (size_t i = 0; i < (size_t)p->nx * p->ny; i++)
+        if (!std::isfinite(phi0_host[i])) {
+            free_ctx(c);
+            return DUGKS_ENONFINITE;
+        }
+    r = upload_plane(c, c->phi0, phi0_host);
+    if (r == DUGKS_OK) r = sync_ctx(c);
+    if (r != DUGKS_OK) {
+        free_ctx(c);
+        return r;
+    }
+    *out = c;
+    return DUGKS_OK;
+}
+
+int dugks_set_velocity(dugks_ctx *c, int kind, const double *params, const double *u_host, const double *v_host) {
+    if (!c) return DUGKS_EINVAL;
+    cudaSetDevice(c->dev);
+    double v[4] = {0, 0, 0, 0};
+    switch (kind) {
+    case DUGKS_VEL_UNIFORM:
+        if (!params) return fail(c, DUGKS_EINVAL, "uniform velocity needs (ux, uy)");
+        v[0] = params[0]; v[1] = params[1];
+        break;
+    case DUGKS_VEL_ROTATION:
+        if (!params) return fail(c, DUGKS_EINVAL, "rotation needs (cx, cy, omega)");
+        v[0] = params[0]; v[1] = params[1]; v[2] = params[2];
+        break;
+    case DUGKS_VEL_VORTEX:
+        if (!params || !(params[0] > 0) || !(params[2] > 0)) return fail(c, DUGKS_EINVAL, "vortex needs (L > 0, U, T > 0)");
+        v[0] = params[0]; v[1] = params[1]; v[2] = params[2];
+        break;
+    case DUGKS_VEL_FIELD: {
+        if (!u_host || !v_host) return fail(c, DUGKS_EINVAL, "field velocity needs u and v arrays");
+        if (!c->ufield) {
+            if (cudaMalloc(&c->ufield, c->plane * c->tsize) != cudaSuccess ||
+                cudaMalloc(&c->vfield, c->plane * c->tsize) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, DUGKS_ENOMEM, "velocity field allocation");
+            }
+        }
+        int r = upload_plane(c, c->ufield, u_host);
+        if (r == DUGKS_OK) r = upload_plane(c, c->vfield, v_host);
+        if (r != DUGKS_OK) return r;
+        break;
+    }
+    default:
+        return fail(c, DUGKS_EINVAL, "unknown velocity kind");
+    }
+    for (int i = 0; i < 4; i++)
+        if (!std::isfinite(v[i])) return fail(c, DUGKS_EINVAL, "velocity parameters must be finite");
+    c->vel_kind = kind;
+    std::memcpy(c->vel, v, sizeof v);
+    if (c->step == 0) c->initialized = false;   // the initial equilibrium depends on u(0)
+    return DUGKS_OK;
+}
+
+int dugks_step(dugks_ctx *c, int64_t nsteps) {
+    if (!c || nsteps < 0) return c ? fail(c, DUGKS_EINVAL, "nsteps < 0") : DUGKS_EINVAL;
+    if (c->sticky != DUGKS_OK) return c->sticky;
+    cudaSetDevice(c->dev);
+    int r = ensure_init(c);
+    for (int64_t s = 0; s < nsteps && r == DUGKS_OK; s++) r = step_once(c);
+    return r;
+}
+
+int dugks_read_phi_device(dugks_ctx *c, void *dev_out) {
+    if (!c || !dev_out) return DUGKS_EINVAL;
+    if (c->sticky != DUGKS_OK) return c->sticky;
+    cudaSetDevice(c->dev);
+    int r = ensure_init(c);
+    if (r == DUGKS_OK) r = enqueue_phi(c, dev_out);
+    return r;
+}
+
+int dugks_read_phi(dugks_ctx *c, double *out_host) {
+    if (!c || !out_host) return DUGKS_EINVAL;
+    int r = dugks_read_phi_device(c, c->tmp);
+    if (r != DUGKS_OK) return r;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    cudaError_t e;
+    if (is_fp64(c)) {
+        e = cudaMemcpyAsync(out_host, c->tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "read phi");
+        return sync_ctx(c);
+    }
+    std::vector<float> tmp(n);
+    e = cudaMemcpyAsync(tmp.data(), c->tmp, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read phi");
+    r = sync_ctx(c);
+    if (r != DUGKS_OK) return r;
+    for (size_t i = 0; i < n; i++) out_host[i] = tmp[i];
+    return DUGKS_OK;
+}
+
+int dugks_mass_device(dugks_ctx *c, double *dev_out) {
+    if (!c || !dev_out) return DUGKS_EINVAL;
+    if (c->sticky != DUGKS_OK) return c->sticky;
+    cudaSetDevice(c->dev);
+    int r = ensure_init(c);
+    if (r == DUGKS_OK) r = enqueue_mass(c, dev_out);
+    return r;
+}
+
+int dugks_mass(dugks_ctx *c, double *out) {
+    if (!c || !out) return DUGKS_EINVAL;
+    int r = dugks_mass_device(c, c->dmass);
+    if (r != DUGKS_OK) return r;
+    cudaError_t e = cudaMemcpyAsync(out, c->dmass, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read mass");
+    r = sync_ctx(c);
+    if (r != DUGKS_OK) return r;
+    if (!std::isfinite(*out)) return fail(c, DUGKS_ENONFINITE, "the field holds NaN or Inf");
+    return DUGKS_OK;
+}
+
+int dugks_status(dugks_ctx *c) {
+    if (!c) return DUGKS_EINVAL;
+    cudaSetDevice(c->dev);
+    int r = sync_ctx(c);
+    if (r != DUGKS_OK) return r;
+    int flags = 0;
+    cudaError_t e = cudaMemcpy(&flags, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+    if (flags & 1) return fail(c, DUGKS_ENONFINITE, "the field holds NaN or Inf");
+    return DUGKS_OK;
+}
+
+const char *dugks_last_error(const dugks_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t dugks_step_index(const dugks_ctx *c) { return c ? c->step : -1; }
+
+static int saved_phi_planes(const dugks_ctx *c) { return c->p.precision == DUGKS_FP16F ? 2 : 1; }
+
+size_t dugks_state_bytes(const dugks_ctx *c) {
+    if (!c) return 0;
+    return 9 * c->plane * c->ssize + (size_t)saved_phi_planes(c) * c->plane * c->tsize;
+}
+
+int dugks_save_state(dugks_ctx *c, void *host, size_t bytes, int64_t *step_index) {
+    if (!c || !host || bytes != dugks_state_bytes(c)) return c ? fail(c, DUGKS_EINVAL, "bad checkpoint buffer") : DUGKS_EINVAL;
+    if (c->sticky != DUGKS_OK) return c->sticky;
+    cudaSetDevice(c->dev);
+    int r = ensure_init(c);
+    if (r != DUGKS_OK) return r;
+    char *h = static_cast<char *>(host);
+    const size_t xs = 9 * c->plane * c->ssize;
+    const void *X = c->p.stages == 3 ? c->X[0] : c->X[c->cur];
+    cudaError_t e = cudaMemcpyAsync(h, X, xs, cudaMemcpyDeviceToHost, c->stream);
+    for (int i = 0; i < saved_phi_planes(c) && e == cudaSuccess; i++)
+        e = cudaMemcpyAsync(h + xs + i * c->plane * c->tsize, c->phi[c->pr[i]], c->plane * c->tsize,
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "save state");
+    if (step_index) *step_index = c->step;
+    return sync_ctx(c);
+}
+
+int dugks_load_state(dugks_ctx *c, const void *host, size_t bytes, int64_t step_index) {
+    if (!c || !host || bytes != dugks_state_bytes(c) || step_index < 0)
+        return c ? fail(c, DUGKS_EINVAL, "bad checkpoint buffer") : DUGKS_EINVAL;
+    if (c->sticky != DUGKS_OK) return c->sticky;
+    cudaSetDevice(c->dev);
+    const char *h = static_cast<const char *>(host);
+    const size_t xs = 9 * c->plane * c->ssize;
+    void *X = c->p.stages == 3 ? c->X[0] : c->X[c->cur];
+    cudaError_t e = cudaMemcpyAsync(X, h, xs, cudaMemcpyHostToDevice, c->stream);
+    for (int i = 0; i < saved_phi_planes(c) && e == cudaSuccess; i++)
+        e = cudaMemcpyAsync(c->phi[c->pr[i]], h + xs + i * c->plane * c->tsize, c->plane * c->tsize,
+                            cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "load state");
+    c->step = step_index;
+    c->initialized = true;
+    c->mass_valid = false;
+    return sync_ctx(c);
+}
+
+void dugks_destroy(dugks_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+}  // extern "C"

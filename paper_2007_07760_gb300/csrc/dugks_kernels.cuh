@@ -1,0 +1,574 @@
+// dugks_kernels.cuh -- device code of the DUGKS time step (sm_103a).
+//
+// Method: Yang, Zhong & Zhuo, "Performance evaluation of high-order
+// reconstruction for discrete unified gas-kinetic scheme in tracking fluid
+// interfaces" (equation numbers are the paper's). Unit cells, D2Q9 with
+// xi_k = e_k (RT = 1/3), tau = 3 M, periodic boundaries.
+//
+// One CTA owns a TX x TY tile of cells. A step (or one stage of the
+// three-stage scheme) is a single fused kernel:
+//   S0  stage the state X (9 SoA planes) of the tile plus a halo of H cells
+//       into shared memory; phi = sum_k X_k                 (Eq. (30))
+//   S1  on the tile plus 1 + R cells: grad phi (isotropic, order p), n, theta,
+//       d(phi u)/dt, source vector V, g_k = f^eq_k + tau S_k and
+//       bar f^+_k = a X_k + b g_k                           (Eqs. (2), (4), (14))
+//   S2  every east / north face of the tile plus one ring: bar f_k at the
+//       back-traced point x_b - xi_k h (upwind Taylor expansion from the
+//       nearest cell, or central), phi_b = sum_k bar f_k, f^eq_b, S_b and the
+//       original f_b                                        (Eqs. (24)-(28))
+//   S3  every cell of the tile: meso-flux L_k (Eq. (21)) and the output
+//       combination out = alpha X + beta g + gamma L (+ accumulator), plus the
+//       cell's phi and an FP64 per-tile mass partial.
+// R is the stencil radius (1 for p <= 3, 2 for p = 4) and H = 1 + 2R.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dugks {
+
+// ---- D2Q9 lattice (Sec. II.B.2) ---------------------------------------------
+__host__ __device__ __forceinline__ constexpr int ex(int k) {
+    return k == 0 ? 0 : (k == 1 || k == 2 || k == 8) ? 1 : (k == 3 || k == 7) ? 0 : -1;
+}
+__host__ __device__ __forceinline__ constexpr int ey(int k) {
+    return k == 0 ? 0 : (k == 2 || k == 3 || k == 4) ? 1 : (k == 1 || k == 5) ? 0 : -1;
+}
+template <typename T>
+__host__ __device__ __forceinline__ constexpr T wq(int k) {
+    return k == 0 ? T(4) / T(9) : (k & 1) ? T(1) / T(9) : T(1) / T(36);
+}
+
+enum Kind { KIND_T2 = 0, KIND_T3A = 1, KIND_T3B = 2 };
+enum Vel { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_FIELD = 3 };
+
+// Storage of the distribution: full values of type T, or (FP16F) half-precision
+// scaled deviations q_k = (f_k - w_k phi) * s / w_k with phi kept as a T plane.
+template <typename T, typename ST>
+struct Store;
+template <typename T>
+struct Store<T, T> {
+    static constexpr bool deviation = false;
+};
+template <>
+struct Store<float, __half> {
+    static constexpr bool deviation = true;
+};
+
+template <typename T>
+struct StepParams {
+    int nx, ny, pitch;          // pitch: elements between rows; planes are ny * pitch apart
+    int tiles_x;                // CTAs along x (mass partial index = by * tiles_x + bx)
+    const void *X;              // 9 planes in (storage type)
+    const void *acc;            // KIND_T3B: accumulator planes (type T)
+    const T *phi_cur;           // deviation storage: phi of X (authoritative)
+    const T *phi_old;           // phi at the older time level of d(phi u)/dt
+    T *phi_out;                 // T2/T3A: phi of X; deviation storage: phi of out1
+    void *out1;                 // 9 planes (storage type for T2/T3B, T for T3A)
+    T *out2;                    // KIND_T3A: accumulator planes
+    double *mass_partial;       // per-CTA sum of phi of out1 (T2, T3B), may be null
+    const T *ufield, *vfield;   // VEL_FIELD cell-centre components
+    T a, b;                     // bar f^+ = a X + b g
+    T h;                        // reconstruction time of the faces
+    T c1, c2, c3;               // f_b = c1 bar f + c2 f^eq_b + c3 S_b   (Eq. (27))
+    T al1, be1, ga1;            // out1 = al1 X + be1 g + ga1 L (+ acc)
+    T al2, be2, ga2;            // out2 = al2 X + be2 g + ga2 L
+    T tau, theta_c, phiA, phiB; // theta = theta_c (phi - phiA)(phi - phiB)   (Eq. (4))
+    T inv_dtD;                  // 1 / (time between phi_old and X)
+    int useD;
+    int vel_kind;
+    T vp0, vp1, vp2;            // velocity parameters
+    T t, t_old, t_face;         // time of X, of phi_old, of the faces
+    T qscale, qinv;             // deviation storage scale s and 1 / s
+};
+
+// ---- prescribed velocity (Sec. II.A; Sec. III) ------------------------------
+template <typename T>
+__device__ __forceinline__ T sinpi_(T x);
+template <>
+__device__ __forceinline__ double sinpi_(double x) { return sinpi(x); }
+template <>
+__device__ __forceinline__ float sinpi_(float x) { return sinpif(x); }
+template <typename T>
+__device__ __forceinline__ T cospi_(T x);
+template <>
+__device__ __forceinline__ double cospi_(double x) { return cospi(x); }
+template <>
+__device__ __forceinline__ float cospi_(float x) { return cospif(x); }
+
+template <typename T>
+__device__ __forceinline__ void vel_analytic(const StepParams<T> &p, T x, T y, T t, T &u, T &v) {
+    if (p.vel_kind == VEL_UNIFORM) {
+        u = p.vp0;
+        v = p.vp1;
+    } else if (p.vel_kind == VEL_ROTATION) {
+        u = -p.vp2 * (y - p.vp1);
+        v = p.vp2 * (x - p.vp0);
+    } else {  // single vortex, period box L, amplitude U, reversal period T
+        const T L = p.vp0, U = p.vp1;
+        const T sx = sinpi_(x / L), sy = sinpi_(y / L), c = cospi_(t / p.vp2);
+        u = -U * sx * sx * sinpi_(T(2) * y / L) * c;
+        v = U * sy * sy * sinpi_(T(2) * x / L) * c;
+    }
+}
+
+// velocity at the centre of cell (gx, gy) (wrapped indices)
+template <typename T>
+__device__ __forceinline__ void vel_cell(const StepParams<T> &p, int gx, int gy, T t, T &u, T &v) {
+    if (p.vel_kind == VEL_FIELD) {
+        const size_t c = (size_t)gy * p.pitch + gx;
+        u = p.ufield[c];
+        v = p.vfield[c];
+    } else {
+        vel_analytic(p, T(gx) + T(0.5), T(gy) + T(0.5), t, u, v);
+    }
+}
+
+// velocity at the east (dir 0: x = gx + 1) or north (dir 1: y = gy + 1) face midpoint
+template <typename T>
+__device__ __forceinline__ void vel_face(const StepParams<T> &p, int gx, int gy, int dir, T t, T &u, T &v) {
+    if (p.vel_kind == VEL_FIELD) {
+        int nxg = gx, nyg = gy;
+        if (dir == 0) nxg = gx + 1 == p.nx ? 0 : gx + 1;
+        else nyg = gy + 1 == p.ny ? 0 : gy + 1;
+        const size_t c0 = (size_t)gy * p.pitch + gx, c1 = (size_t)nyg * p.pitch + nxg;
+        u = T(0.5) * (p.ufield[c0] + p.ufield[c1]);
+        v = T(0.5) * (p.vfield[c0] + p.vfield[c1]);
+    } else if (dir == 0) {
+        vel_analytic(p, T(gx) + T(1), T(gy) + T(0.5), t, u, v);
+    } else {
+        vel_analytic(p, T(gx) + T(0.5), T(gy) + T(1), t, u, v);
+    }
+}
+
+// ---- isotropic finite differences (Sec. II.B.1, II.B.2) ----------------------
+// F points at the centre value of a shared-memory plane with row stride ld.
+#define FA(dx, dy) F[(dy) * ld + (dx)]
+
+// Lattice-moment gradient (1/cs^2) sum_k w_k e_k F(x + e_k): leading error
+// (1/6) grad lap F, isotropic.
+template <typename T>
+__device__ __forceinline__ void grad9(const T *F, int ld, T &gx, T &gy) {
+    const T ne = FA(1, 1), nw = FA(-1, 1), se = FA(1, -1), sw = FA(-1, -1);
+    gx = (FA(1, 0) - FA(-1, 0)) * T(1.0 / 3.0) + ((ne - nw) + (se - sw)) * T(1.0 / 12.0);
+    gy = (FA(0, 1) - FA(0, -1)) * T(1.0 / 3.0) + ((ne - se) + (nw - sw)) * T(1.0 / 12.0);
+}
+
+// Lattice-moment Hessian (1/cs^4) sum_k w_k (e_a e_b - cs^2 delta_ab) F(x + s e_k) / s^2.
+template <typename T, int S>
+__device__ __forceinline__ void hess9(const T *F, int ld, T &hxx, T &hxy, T &hyy) {
+    const T c = FA(0, 0);
+    const T ew = FA(S, 0) + FA(-S, 0), ns = FA(0, S) + FA(0, -S);
+    const T ne = FA(S, S), nw = FA(-S, S), se = FA(S, -S), sw = FA(-S, -S);
+    const T cor = (ne + nw) + (se + sw);
+    constexpr T inv = T(1) / T(S * S);
+    hxx = (T(2.0 / 3.0) * ew - T(1.0 / 3.0) * ns + T(1.0 / 6.0) * cor - T(4.0 / 3.0) * c) * inv;
+    hyy = (T(2.0 / 3.0) * ns - T(1.0 / 3.0) * ew + T(1.0 / 6.0) * cor - T(4.0 / 3.0) * c) * inv;
+    hxy = ((ne - nw) - (se - sw)) * T(0.25) * inv;
+}
+
+// Fourth-order gradient on the 5x5 block without corners, with isotropic
+// fifth-order error: weights 13/30, 2/15, -1/60 (at (1, +-2)), -1/60 (at (2, 0)),
+// -1/30 (at (2, +-1)), antisymmetric along the derivative.
+template <typename T>
+__device__ __forceinline__ void grad21(const T *F, int ld, T &gx, T &gy) {
+    gx = T(13.0 / 30.0) * (FA(1, 0) - FA(-1, 0)) +
+         T(2.0 / 15.0) * ((FA(1, 1) - FA(-1, 1)) + (FA(1, -1) - FA(-1, -1))) -
+         T(1.0 / 60.0) * ((FA(1, 2) - FA(-1, 2)) + (FA(1, -2) - FA(-1, -2))) -
+         T(1.0 / 60.0) * (FA(2, 0) - FA(-2, 0)) -
+         T(1.0 / 30.0) * ((FA(2, 1) - FA(-2, 1)) + (FA(2, -1) - FA(-2, -1)));
+    gy = T(13.0 / 30.0) * (FA(0, 1) - FA(0, -1)) +
+         T(2.0 / 15.0) * ((FA(1, 1) - FA(1, -1)) + (FA(-1, 1) - FA(-1, -1))) -
+         T(1.0 / 60.0) * ((FA(2, 1) - FA(2, -1)) + (FA(-2, 1) - FA(-2, -1))) -
+         T(1.0 / 60.0) * (FA(0, 2) - FA(0, -2)) -
+         T(1.0 / 30.0) * ((FA(1, 2) - FA(1, -2)) + (FA(-1, 2) - FA(-1, -2)));
+}
+
+template <typename T, int ORDER>
+__device__ __forceinline__ void grad_p(const T *F, int ld, T &gx, T &gy) {
+    if constexpr (ORDER == 4) grad21(F, ld, gx, gy);
+    else grad9(F, ld, gx, gy);
+}
+
+// Taylor expansion about the cell at F evaluated at displacement (dx, dy):
+// value + d.grad (+ 1/2 d d : H for p >= 3) (+ 1/6 d d d : T for p = 4).
+template <typename T, int ORDER>
+__device__ __forceinline__ T taylor(const T *F, int ld, T dx, T dy) {
+    T gx, gy;
+    grad_p<T, ORDER>(F, ld, gx, gy);
+    T v = FA(0, 0) + dx * gx + dy * gy;
+    if constexpr (ORDER >= 3) {
+        T hxx, hxy, hyy;
+        if constexpr (ORDER == 4) {
+            // (4 H_1 - H_2) / 3: fourth order
+            T axx, axy, ayy, bxx, bxy, byy;
+            hess9<T, 1>(F, ld, axx, axy, ayy);
+            hess9<T, 2>(F, ld, bxx, bxy, byy);
+            hxx = T(4.0 / 3.0) * axx - T(1.0 / 3.0) * bxx;
+            hxy = T(4.0 / 3.0) * axy - T(1.0 / 3.0) * bxy;
+            hyy = T(4.0 / 3.0) * ayy - T(1.0 / 3.0) * byy;
+        } else {
+            hess9<T, 1>(F, ld, hxx, hxy, hyy);
+        }
+        v += T(0.5) * (dx * dx * hxx + T(2) * dx * dy * hxy + dy * dy * hyy);
+    }
+    if constexpr (ORDER == 4) {
+        // second-order third derivatives (products of central differences)
+        const T txxx = T(0.5) * (FA(2, 0) - FA(-2, 0)) - (FA(1, 0) - FA(-1, 0));
+        const T tyyy = T(0.5) * (FA(0, 2) - FA(0, -2)) - (FA(0, 1) - FA(0, -1));
+        const T txxy = T(0.5) * ((FA(1, 1) - FA(1, -1)) + (FA(-1, 1) - FA(-1, -1))) - (FA(0, 1) - FA(0, -1));
+        const T txyy = T(0.5) * ((FA(1, 1) - FA(-1, 1)) + (FA(1, -1) - FA(-1, -1))) - (FA(1, 0) - FA(-1, 0));
+        v += (dx * dx * dx * txxx + T(3) * dx * dx * dy * txxy + T(3) * dx * dy * dy * txyy +
+              dy * dy * dy * tyyy) * T(1.0 / 6.0);
+    }
+    return v;
+}
+#undef FA
+
+// ---- block reduction in FP64 (fixed order: deterministic) -------------------
+__device__ __forceinline__ double block_sum(double v, double *sred) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sred[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 0; w < nw; w++) s += sred[w];
+    }
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+template <typename ST>
+__device__ __forceinline__ float to_f(ST v);
+template <>
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
+// ---- the fused step kernel ----------------------------------------------------
+template <typename T, typename ST, int ORDER, int FLUX, int KIND, int TX, int TY>
+struct Tile {
+    static constexpr int R = ORDER == 4 ? 2 : 1;
+    static constexpr int H = 1 + 2 * R;
+    static constexpr int WH = TX + 2 * H, HH = TY + 2 * H;          // state region
+    static constexpr int WC = TX + 2 + 2 * R, HC = TY + 2 + 2 * R;  // cell-quantity region
+    static constexpr int WF = TX + 1, HF = TY + 1;                  // face owners
+    static constexpr int NH = WH * HH, NC = WC * HC, NF = WF * HF;
+    static constexpr size_t red_offset = (sizeof(T) * (size_t)(9 * NH + NH + 9 * NC + 4 * NC + 18 * NF) + 15) / 16 * 16;
+    static constexpr size_t smem_bytes = red_offset + 64 * sizeof(double);
+};
+
+template <typename T, typename ST, int ORDER, int FLUX, int KIND, int TX, int TY>
+__global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
+    using TL = Tile<T, ST, ORDER, FLUX, KIND, TX, TY>;
+    constexpr int R = TL::R, H = TL::H, WH = TL::WH, WC = TL::WC, WF = TL::WF;
+    constexpr int NH = TL::NH, NC = TL::NC, NF = TL::NF;
+    constexpr bool DEV = Store<T, ST>::deviation;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sX = reinterpret_cast<T *>(smem_raw);  // [9][NH]
+    T *sPhi = sX + 9 * NH;                    // [NH]
+    T *sFbp = sPhi + NH;                      // [9][NC]
+    T *sV = sFbp + 9 * NC;                    // [2][NC]
+    T *sP = sV + 2 * NC;                      // [2][NC]
+    T *sFb = sP + 2 * NC;                     // [9][2][NF]
+    double *sred = reinterpret_cast<double *>(smem_raw + TL::red_offset);
+
+    const int nx = p.nx, ny = p.ny, pitch = p.pitch;
+    const size_t plane = (size_t)ny * pitch;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // S0: state + halo -> shared memory; phi of X
+    for (int idx = tid; idx < NH; idx += nt) {
+        const int ly = idx / WH, lx = idx - ly * WH;
+        int gx = x0 - H + lx, gy = y0 - H + ly;
+        gx = (gx % nx + nx) % nx;
+        gy = (gy % ny + ny) % ny;
+        const size_t g = (size_t)gy * pitch + gx;
+        if constexpr (DEV) {
+            const __half *Xq = static_cast<const __half *>(p.X);
+            const T ph = p.phi_cur[g];
+#pragma unroll
+            for (int k = 0; k < 9; k++) sX[k * NH + idx] = wq<T>(k) * (ph + to_f(Xq[k * plane + g]) * p.qinv);
+            sPhi[idx] = ph;
+        } else {
+            const T *Xf = static_cast<const T *>(p.X);
+            T ph = T(0);
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const T v = Xf[k * plane + g];
+                sX[k * NH + idx] = v;
+                ph += v;
+            }
+            sPhi[idx] = ph;
+        }
+    }
+    __syncthreads();
+
+    // S1: cell quantities and bar f^+ on the tile plus 1 + R cells
+    for (int idx = tid; idx < NC; idx += nt) {
+        const int ly = idx / WC, lx = idx - ly * WC;
+        const int rx = lx - (1 + R), ry = ly - (1 + R);       // relative to the tile origin
+        const int hidx = (ry + H) * WH + (rx + H);
+        int gx = x0 + rx, gy = y0 + ry;
+        gx = (gx % nx + nx) % nx;
+        gy = (gy % ny + ny) % ny;
+        const T ph = sPhi[hidx];
+        T gxp, gyp;
+        grad_p<T, ORDER>(sPhi + hidx, WH, gxp, gyp);
+        const T g2 = gxp * gxp + gyp * gyp;
+        T nxv = T(0), nyv = T(0);
+        if (g2 > T(1e-24)) {  // n = grad phi / |grad phi| (Eq. (2)); n = 0 where it vanishes
+            const T inv = T(1) / sqrt(g2);
+            nxv = gxp * inv;
+            nyv = gyp * inv;
+        }
+        const T theta = p.theta_c * (ph - p.phiA) * (ph - p.phiB);  // Eq. (4)
+        T u, v;
+        vel_cell(p, gx, gy, p.t, u, v);
+        T Dx = T(0), Dy = T(0);
+        if (p.useD) {  // d(phi u)/dt, backward difference
+            T uo, vo;
+            vel_cell(p, gx, gy, p.t_old, uo, vo);
+            const T po = p.phi_old[(size_t)gy * pitch + gx];
+            Dx = (ph * u - po * uo) * p.inv_dtD;
+            Dy = (ph * v - po * vo) * p.inv_dtD;
+        }
+        // S_k = w_k xi_k . V with V = theta n + D / RT           (Eq. (14b))
+        const T Vx = theta * nxv + T(3) * Dx, Vy = theta * nyv + T(3) * Dy;
+        // g_k = f^eq_k + tau S_k = w_k (phi + xi_k . P),  P = phi u / RT + tau V
+        const T Px = T(3) * ph * u + p.tau * Vx, Py = T(3) * ph * v + p.tau * Vy;
+        sV[idx] = Vx;
+        sV[NC + idx] = Vy;
+        sP[idx] = Px;
+        sP[NC + idx] = Py;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const T gk = wq<T>(k) * (ph + (T(ex(k)) * Px + T(ey(k)) * Py));
+            sFbp[k * NC + idx] = p.a * sX[k * NH + hidx] + p.b * gk;
+        }
+    }
+    __syncthreads();
+
+    // S2: faces. Owner cell (fx, fy) in [-1, TX) x [-1, TY) computes its east and
+    // north faces.
+    for (int idx = tid; idx < NF; idx += nt) {
+        const int fy = idx / WF - 1, fx = idx - (fy + 1) * WF - 1;
+        const int ci = (fy + 1 + R) * WC + (fx + 1 + R);  // owner in the cell-quantity region
+        const int cE = ci + 1, cN = ci + WC;
+        T fe[9], fn[9];
+        T phE = T(0), phN = T(0);
+        const T h = p.h;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const T *F = sFbp + k * NC;
+            const T exk = T(ex(k)), eyk = T(ey(k));
+            T vE, vN;
+            if constexpr (FLUX == 0) {
+                // Upwind (Eq. (26)): expand about the cell centre nearest to
+                // x_b - xi h; a tie (xi normal to the face = 0) averages both sides.
+                if (ex(k) > 0) vE = taylor<T, ORDER>(F + ci, WC, T(0.5) - h, -eyk * h);
+                else if (ex(k) < 0) vE = taylor<T, ORDER>(F + cE, WC, h - T(0.5), -eyk * h);
+                else vE = T(0.5) * (taylor<T, ORDER>(F + ci, WC, T(0.5), -eyk * h) +
+                                    taylor<T, ORDER>(F + cE, WC, T(-0.5), -eyk * h));
+                if (ey(k) > 0) vN = taylor<T, ORDER>(F + ci, WC, -exk * h, T(0.5) - h);
+                else if (ey(k) < 0) vN = taylor<T, ORDER>(F + cN, WC, -exk * h, h - T(0.5));
+                else vN = T(0.5) * (taylor<T, ORDER>(F + ci, WC, -exk * h, T(0.5)) +
+                                    taylor<T, ORDER>(F + cN, WC, -exk * h, T(-0.5)));
+            } else {
+                // Central (Eq. (25)): face mean, normal difference, mean tangential derivative.
+                T gxc, gyc, gxe, gye, gxn, gyn;
+                grad_p<T, ORDER>(F + ci, WC, gxc, gyc);
+                grad_p<T, ORDER>(F + cE, WC, gxe, gye);
+                grad_p<T, ORDER>(F + cN, WC, gxn, gyn);
+                const T Fc = F[ci], Fe = F[cE], Fn = F[cN];
+                vE = T(0.5) * (Fc + Fe) - h * (exk * (Fe - Fc) + eyk * (T(0.5) * (gyc + gye)));
+                vN = T(0.5) * (Fc + Fn) - h * (exk * (T(0.5) * (gxc + gxn)) + eyk * (Fn - Fc));
+            }
+            fe[k] = vE;
+            fn[k] = vN;
+            phE += vE;
+            phN += vN;
+        }
+        int gx = x0 + fx, gy = y0 + fy;
+        gx = (gx % nx + nx) % nx;
+        gy = (gy % ny + ny) % ny;
+        T uE, vE_, uN, vN_;
+        vel_face(p, gx, gy, 0, p.t_face, uE, vE_);
+        vel_face(p, gx, gy, 1, p.t_face, uN, vN_);
+        // face source: mean of the two cells at the base time
+        const T VxE = T(0.5) * (sV[ci] + sV[cE]), VyE = T(0.5) * (sV[NC + ci] + sV[NC + cE]);
+        const T VxN = T(0.5) * (sV[ci] + sV[cN]), VyN = T(0.5) * (sV[NC + ci] + sV[NC + cN]);
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const T exk = T(ex(k)), eyk = T(ey(k)), w = wq<T>(k);
+            const T feqE = w * phE * (T(1) + T(3) * (exk * uE + eyk * vE_));
+            const T feqN = w * phN * (T(1) + T(3) * (exk * uN + eyk * vN_));
+            const T SE = w * (exk * VxE + eyk * VyE), SN = w * (exk * VxN + eyk * VyN);
+            sFb[(2 * k) * NF + idx] = p.c1 * fe[k] + p.c2 * feqE + p.c3 * SE;
+            sFb[(2 * k + 1) * NF + idx] = p.c1 * fn[k] + p.c2 * feqN + p.c3 * SN;
+        }
+    }
+    __syncthreads();
+
+    // S3: flux and update of the tile's own cells
+    double msum = 0.0;
+    for (int idx = tid; idx < TX * TY; idx += nt) {
+        const int ly = idx / TX, lx = idx - ly * TX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= nx || gy >= ny) continue;
+        const size_t g = (size_t)gy * pitch + gx;
+        const int hidx = (ly + H) * WH + (lx + H);
+        const int cidx = (ly + 1 + R) * WC + (lx + 1 + R);
+        const int fidx = (ly + 1) * WF + (lx + 1);
+        const T ph = sPhi[hidx], Px = sP[cidx], Py = sP[NC + cidx];
+        T o1[9];
+        T phn = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const T gk = wq<T>(k) * (ph + (T(ex(k)) * Px + T(ey(k)) * Py));
+            const T *fE = sFb + (2 * k) * NF, *fN = sFb + (2 * k + 1) * NF;
+            // Eq. (21) with the outward normal of a unit cell
+            const T L = -(T(ex(k)) * (fE[fidx] - fE[fidx - 1]) + T(ey(k)) * (fN[fidx] - fN[fidx - WF]));
+            const T Xk = sX[k * NH + hidx];
+            T v = p.al1 * Xk + p.be1 * gk + p.ga1 * L;
+            if constexpr (KIND == KIND_T3B) v += static_cast<const T *>(p.acc)[k * plane + g];
+            if constexpr (KIND == KIND_T3A) p.out2[k * plane + g] = p.al2 * Xk + p.be2 * gk + p.ga2 * L;
+            o1[k] = v;
+            phn += v;
+        }
+        if constexpr (DEV) {
+            __half *Oq = static_cast<__half *>(p.out1);
+#pragma unroll
+            for (int k = 0; k < 9; k++)
+                Oq[k * plane + g] = __float2half_rn((o1[k] - wq<T>(k) * phn) * (p.qscale * (T(1) / wq<T>(k))));
+            p.phi_out[g] = phn;
+            msum += (double)phn;
+        } else {
+            T *O = static_cast<T *>(p.out1);
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                O[k * plane + g] = o1[k];
+                s += (double)o1[k];
+            }
+            if (KIND != KIND_T3B) p.phi_out[g] = ph;
+            msum += s;
+        }
+    }
+    if (p.mass_partial != nullptr) {
+        const double s = block_sum(msum, sred);
+        if (tid == 0) p.mass_partial[blockIdx.y * p.tiles_x + blockIdx.x] = s;
+    }
+}
+
+// ---- initial state: f = f^eq (Omega = 0), D = 0 ------------------------------
+// X = f^eq - frac * dt * S with frac = 1/2 (two-stage tilde f) or 1/4 (hat f).
+template <typename T, typename ST, int ORDER>
+__global__ void init_kernel(const StepParams<T> p, const T *phi0, T frac_dt) {
+    constexpr bool DEV = Store<T, ST>::deviation;
+    constexpr int R = ORDER == 4 ? 2 : 1;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+    if (gx >= p.nx || gy >= p.ny) return;
+    const int nx = p.nx, ny = p.ny, pitch = p.pitch;
+    const size_t plane = (size_t)ny * pitch;
+    // gather the (2R+1)^2 neighbourhood of phi0 into registers
+    T nb[(2 * R + 1) * (2 * R + 1)];
+#pragma unroll
+    for (int dy = -R; dy <= R; dy++)
+#pragma unroll
+        for (int dx = -R; dx <= R; dx++) {
+            const int xx = (gx + dx + nx) % nx, yy = (gy + dy + ny) % ny;
+            nb[(dy + R) * (2 * R + 1) + (dx + R)] = phi0[(size_t)yy * pitch + xx];
+        }
+    const T *c = nb + R * (2 * R + 1) + R;
+    T gxp, gyp;
+    grad_p<T, ORDER>(c, 2 * R + 1, gxp, gyp);
+    const T ph = *c;
+    const T g2 = gxp * gxp + gyp * gyp;
+    T nxv = T(0), nyv = T(0);
+    if (g2 > T(1e-24)) {
+        const T inv = T(1) / sqrt(g2);
+        nxv = gxp * inv;
+        nyv = gyp * inv;
+    }
+    const T theta = p.theta_c * (ph - p.phiA) * (ph - p.phiB);
+    T u, v;
+    vel_cell(p, gx, gy, p.t, u, v);
+    const T Vx = theta * nxv, Vy = theta * nyv;
+    const size_t g = (size_t)gy * pitch + gx;
+    T fk[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        const T exk = T(ex(k)), eyk = T(ey(k)), w = wq<T>(k);
+        const T feq = w * ph * (T(1) + T(3) * (exk * u + eyk * v));
+        const T S = w * (exk * Vx + eyk * Vy);
+        fk[k] = feq - frac_dt * S;
+    }
+    if constexpr (DEV) {
+        // phi of X: sum of the distribution (equals phi0 up to rounding)
+        T phn = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; k++) phn += fk[k];
+        __half *Oq = static_cast<__half *>(p.out1);
+#pragma unroll
+        for (int k = 0; k < 9; k++)
+            Oq[k * plane + g] = __float2half_rn((fk[k] - wq<T>(k) * phn) * (p.qscale * (T(1) / wq<T>(k))));
+        p.phi_out[g] = phn;
+    } else {
+        T *O = static_cast<T *>(p.out1);
+#pragma unroll
+        for (int k = 0; k < 9; k++) O[k * plane + g] = fk[k];
+    }
+}
+
+// ---- mass: per-tile FP64 partials in the step kernels' tiling, then one CTA --
+template <typename T, typename ST, int TX, int TY>
+__global__ void __launch_bounds__(256) mass_partial_kernel(const StepParams<T> p) {
+    __shared__ double sred[32];
+    constexpr bool DEV = Store<T, ST>::deviation;
+    const size_t plane = (size_t)p.ny * p.pitch;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    double msum = 0.0;
+    for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
+        const int ly = idx / TX, lx = idx - ly * TX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= p.nx || gy >= p.ny) continue;
+        const size_t g = (size_t)gy * p.pitch + gx;
+        if constexpr (DEV) {
+            msum += (double)p.phi_cur[g];
+        } else {
+            const T *Xf = static_cast<const T *>(p.X);
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 9; k++) s += (double)Xf[k * plane + g];
+            msum += s;
+        }
+    }
+    const double s = block_sum(msum, sred);
+    if (threadIdx.x == 0) p.mass_partial[blockIdx.y * p.tiles_x + blockIdx.x] = s;
+}
+
+// phi of the state into a T plane (pitch-free, ny * nx)
+template <typename T, typename ST>
+__global__ void phi_kernel(const StepParams<T> p, T *out) {
+    constexpr bool DEV = Store<T, ST>::deviation;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+    if (gx >= p.nx || gy >= p.ny) return;
+    const size_t g = (size_t)gy * p.pitch + gx;
+    const size_t plane = (size_t)p.ny * p.pitch;
+    T ph;
+    if constexpr (DEV) {
+        ph = p.phi_cur[g];
+    } else {
+        const T *Xf = static_cast<const T *>(p.X);
+        ph = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; k++) ph += Xf[k * plane + g];
+    }
+    out[(size_t)gy * p.nx + gx] = ph;
+}
+
+}  // namespace dugks

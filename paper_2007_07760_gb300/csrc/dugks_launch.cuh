@@ -1,0 +1,81 @@
+// dugks_launch.cuh -- launchers of one precision; included once by each
+// dugks_inst_*.cu so the three precisions compile in parallel.
+#pragma once
+
+#include "dugks_internal.h"
+
+namespace dugks {
+
+template <typename T, typename ST, int ORDER, int FLUX, int KIND>
+static cudaError_t launch_step_t(const StepParams<T> &p, cudaStream_t s) {
+    using TL = Tile<T, ST, ORDER, FLUX, KIND, TILE_X, TILE_Y>;
+    auto kern = step_kernel<T, ST, ORDER, FLUX, KIND, TILE_X, TILE_Y>;
+    static bool configured = false;   // per instantiation; the attribute is per function
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)TL::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TILE_Y - 1) / TILE_Y);
+    kern<<<grid, STEP_THREADS, TL::smem_bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T, typename ST, int ORDER, int FLUX>
+static cudaError_t launch_kind(const StepParams<T> &p, int kind, cudaStream_t s) {
+    if constexpr (Store<T, ST>::deviation) {
+        if (kind != KIND_T2) return cudaErrorInvalidValue;
+        return launch_step_t<T, ST, ORDER, FLUX, KIND_T2>(p, s);
+    } else {
+        switch (kind) {
+        case KIND_T2: return launch_step_t<T, ST, ORDER, FLUX, KIND_T2>(p, s);
+        case KIND_T3A: return launch_step_t<T, ST, ORDER, FLUX, KIND_T3A>(p, s);
+        case KIND_T3B: return launch_step_t<T, ST, ORDER, FLUX, KIND_T3B>(p, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+}
+
+template <typename T, typename ST, int ORDER>
+static cudaError_t launch_flux(const StepParams<T> &p, int flux, int kind, cudaStream_t s) {
+    return flux == 0 ? launch_kind<T, ST, ORDER, 0>(p, kind, s) : launch_kind<T, ST, ORDER, 1>(p, kind, s);
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::step(const StepParams<T> &p, int order, int flux, int kind, cudaStream_t s) {
+    switch (order) {
+    case 2: return launch_flux<T, ST, 2>(p, flux, kind, s);
+    case 3: return launch_flux<T, ST, 3>(p, flux, kind, s);
+    case 4: return launch_flux<T, ST, 4>(p, flux, kind, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::init(const StepParams<T> &p, const T *phi0, T frac_dt, int order, cudaStream_t s) {
+    dim3 block(128), grid((p.nx + 127) / 128, p.ny);
+    switch (order) {
+    case 2: init_kernel<T, ST, 2><<<grid, block, 0, s>>>(p, phi0, frac_dt); break;
+    case 3: init_kernel<T, ST, 3><<<grid, block, 0, s>>>(p, phi0, frac_dt); break;
+    case 4: init_kernel<T, ST, 4><<<grid, block, 0, s>>>(p, phi0, frac_dt); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::mass_partial(const StepParams<T> &p, cudaStream_t s) {
+    dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TILE_Y - 1) / TILE_Y);
+    mass_partial_kernel<T, ST, TILE_X, TILE_Y><<<grid, STEP_THREADS, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::phi(const StepParams<T> &p, T *out, cudaStream_t s) {
+    dim3 block(128), grid((p.nx + 127) / 128, p.ny);
+    phi_kernel<T, ST><<<grid, block, 0, s>>>(p, out);
+    return cudaGetLastError();
+}
+
+}  // namespace dugks

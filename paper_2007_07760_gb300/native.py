@@ -1,0 +1,241 @@
+"""Thin ctypes binding of libdugks.so (declared in include/dugks.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+the library. There is no CPU fallback: if the library cannot be loaded, or no
+CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+DUGKS_OK, DUGKS_EINVAL, DUGKS_ENOMEM, DUGKS_ECUDA, DUGKS_ETIMEOUT, DUGKS_ENONFINITE, DUGKS_ESTATE = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "ESTATE"}
+DUGKS_FP64, DUGKS_FP32, DUGKS_FP16F = 0, 1, 2
+DUGKS_UPWIND, DUGKS_CENTRAL = 0, 1
+DUGKS_VEL_UNIFORM, DUGKS_VEL_ROTATION, DUGKS_VEL_VORTEX, DUGKS_VEL_FIELD = 0, 1, 2, 3
+PRECISIONS = {"fp64": DUGKS_FP64, "fp32": DUGKS_FP32, "fp16f": DUGKS_FP16F}
+VEL_KINDS = {"uniform": 0, "rotation": 1, "vortex": 2, "field": 3}
+
+
+class dugks_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("W", ctypes.c_double), ("M", ctypes.c_double), ("cfl", ctypes.c_double),
+        ("order", ctypes.c_int32), ("flux", ctypes.c_int32), ("stages", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("dtphiu", ctypes.c_int32),
+        ("phiA", ctypes.c_double), ("phiB", ctypes.c_double),
+    ]
+
+
+class DugksError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        super().__init__(f"dugks error {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/dugks.h
+_VP, _DP, _I64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+SIGNATURES = [
+    ("dugks_create", ctypes.c_int, [ctypes.POINTER(dugks_params), _DP, _VP, ctypes.POINTER(_VP)]),
+    ("dugks_set_velocity", ctypes.c_int, [_VP, ctypes.c_int, _DP, _DP, _DP]),
+    ("dugks_step", ctypes.c_int, [_VP, _I64]),
+    ("dugks_read_phi", ctypes.c_int, [_VP, _DP]),
+    ("dugks_read_phi_device", ctypes.c_int, [_VP, _VP]),
+    ("dugks_mass", ctypes.c_int, [_VP, _DP]),
+    ("dugks_mass_device", ctypes.c_int, [_VP, _VP]),
+    ("dugks_status", ctypes.c_int, [_VP]),
+    ("dugks_last_error", ctypes.c_char_p, [_VP]),
+    ("dugks_step_index", _I64, [_VP]),
+    ("dugks_state_bytes", ctypes.c_size_t, [_VP]),
+    ("dugks_save_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(_I64)]),
+    ("dugks_load_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _I64]),
+    ("dugks_destroy", None, [_VP]),
+]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdugks.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(ctx, code: int):
+    if code != DUGKS_OK:
+        msg = lib().dugks_last_error(ctx).decode() if ctx else ""
+        raise DugksError(code, msg)
+
+
+# ---- the C entry points under the same names --------------------------------
+
+def dugks_create(params: dugks_params, phi0: np.ndarray, stream: int | None = None):
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    if phi0.shape != (params.ny, params.nx):
+        raise ValueError("phi0 must be (ny, nx)")
+    out = ctypes.c_void_p()
+    code = lib().dugks_create(ctypes.byref(params), _dptr(phi0), ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    _check(None, code)
+    return out.value
+
+
+def dugks_set_velocity(ctx, kind: int, params=None, u: np.ndarray | None = None, v: np.ndarray | None = None):
+    p = np.ascontiguousarray(list(params or []) + [0.0] * 4, dtype=np.float64)
+    up = vp = None
+    if u is not None:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        up, vp = _dptr(u), _dptr(v)
+    _check(ctx, lib().dugks_set_velocity(ctx, kind, _dptr(p), up, vp))
+
+
+def dugks_step(ctx, nsteps: int):
+    _check(ctx, lib().dugks_step(ctx, int(nsteps)))
+
+
+def dugks_read_phi(ctx, out: np.ndarray):
+    _check(ctx, lib().dugks_read_phi(ctx, _dptr(out)))
+    return out
+
+
+def dugks_read_phi_device(ctx, dev_ptr: int):
+    _check(ctx, lib().dugks_read_phi_device(ctx, ctypes.c_void_p(dev_ptr)))
+
+
+def dugks_mass(ctx) -> float:
+    m = ctypes.c_double()
+    _check(ctx, lib().dugks_mass(ctx, ctypes.byref(m)))
+    return m.value
+
+
+def dugks_mass_device(ctx, dev_ptr: int):
+    _check(ctx, lib().dugks_mass_device(ctx, ctypes.c_void_p(dev_ptr)))
+
+
+def dugks_status(ctx) -> int:
+    return lib().dugks_status(ctx)
+
+
+def dugks_last_error(ctx) -> str:
+    return lib().dugks_last_error(ctx).decode()
+
+
+def dugks_step_index(ctx) -> int:
+    return lib().dugks_step_index(ctx)
+
+
+def dugks_state_bytes(ctx) -> int:
+    return lib().dugks_state_bytes(ctx)
+
+
+def dugks_save_state(ctx, buf) -> int:
+    """buf: a writable buffer (numpy uint8 array, or an address with .nbytes)."""
+    idx = ctypes.c_int64()
+    addr, n = _buf(buf)
+    _check(ctx, lib().dugks_save_state(ctx, ctypes.c_void_p(addr), n, ctypes.byref(idx)))
+    return idx.value
+
+
+def dugks_load_state(ctx, buf, step_index: int):
+    addr, n = _buf(buf)
+    _check(ctx, lib().dugks_load_state(ctx, ctypes.c_void_p(addr), n, int(step_index)))
+
+
+def dugks_destroy(ctx):
+    if ctx:
+        lib().dugks_destroy(ctx)
+
+
+def _buf(buf):
+    if isinstance(buf, np.ndarray):
+        assert buf.flags["C_CONTIGUOUS"]
+        return buf.ctypes.data, buf.nbytes
+    # torch tensor (e.g. pinned host memory)
+    return buf.data_ptr(), buf.numel() * buf.element_size()
+
+
+def make_params(nx, ny, W=4.0, M=0.01, cfl=0.8, order=2, flux=0, stages=2, precision="fp64",
+                dtphiu=1, phiA=1.0, phiB=0.0) -> dugks_params:
+    p = dugks_params()
+    p.nx, p.ny, p.W, p.M, p.cfl = nx, ny, W, M, cfl
+    p.order, p.flux, p.stages = order, flux, stages
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+    p.dtphiu, p.phiA, p.phiB = dtphiu, phiA, phiB
+    return p
+
+
+class Solver:
+    """Owning wrapper of one context: create, set velocity, step, read."""
+
+    def __init__(self, nx, ny, phi0, *, vel_kind="uniform", vel=(0.0, 0.0), u=None, v=None,
+                 stream: int | None = None, **kw):
+        self.params = make_params(nx, ny, **kw)
+        self.ctx = dugks_create(self.params, phi0, stream)
+        try:
+            dugks_set_velocity(self.ctx, VEL_KINDS[vel_kind], vel, u, v)
+        except Exception:
+            self.close()
+            raise
+
+    @classmethod
+    def from_problem(cls, prob, precision="fp64", stream=None):
+        return cls(prob.nx, prob.ny, prob.phi0, vel_kind=prob.vel_kind, vel=prob.vel, W=prob.W, M=prob.M,
+                   cfl=prob.cfl, order=prob.order, flux=prob.flux, stages=prob.stages,
+                   precision=precision, dtphiu=prob.dtphiu, stream=stream)
+
+    def step(self, n=1):
+        dugks_step(self.ctx, n)
+        return self
+
+    def phi(self) -> np.ndarray:
+        out = np.empty((self.params.ny, self.params.nx))
+        return dugks_read_phi(self.ctx, out)
+
+    def mass(self) -> float:
+        return dugks_mass(self.ctx)
+
+    @property
+    def step_index(self) -> int:
+        return dugks_step_index(self.ctx)
+
+    def status(self) -> int:
+        return dugks_status(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            dugks_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
