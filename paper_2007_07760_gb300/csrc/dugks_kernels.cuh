@@ -347,7 +347,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             const T gk = wq<T>(k) * (ph + (T(ex(k)) * Px + T(ey(k)) * Py));
-            sFbp[k * NC + idx] = p.a * sX[k * NH + hidx] + p.b * gk;
+            // a + b = 1: written as an increment so FP32 keeps the non-equilibrium part
+            const T xk = sX[k * NH + hidx];
+            sFbp[k * NC + idx] = xk + p.b * (gk - xk);
         }
     }
     __syncthreads();
@@ -407,8 +409,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             const T feqE = w * phE * (T(1) + T(3) * (exk * uE + eyk * vE_));
             const T feqN = w * phN * (T(1) + T(3) * (exk * uN + eyk * vN_));
             const T SE = w * (exk * VxE + eyk * VyE), SN = w * (exk * VxN + eyk * VyN);
-            sFb[(2 * k) * NF + idx] = p.c1 * fe[k] + p.c2 * feqE + p.c3 * SE;
-            sFb[(2 * k + 1) * NF + idx] = p.c1 * fn[k] + p.c2 * feqN + p.c3 * SN;
+            // c1 + c2 = 1: f_b = bar f + c2 (f^eq_b - bar f) + c3 S_b
+            sFb[(2 * k) * NF + idx] = fe[k] + p.c2 * (feqE - fe[k]) + p.c3 * SE;
+            sFb[(2 * k + 1) * NF + idx] = fn[k] + p.c2 * (feqN - fn[k]) + p.c3 * SN;
         }
     }
     __syncthreads();
@@ -424,8 +427,13 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
         const int cidx = (ly + 1 + R) * WC + (lx + 1 + R);
         const int fidx = (ly + 1) * WF + (lx + 1);
         const T ph = sPhi[hidx], Px = sP[cidx], Py = sP[NC + cidx];
-        T o1[9];
-        T phn = T(0);
+        // out = base + beta (g - X) + gamma L with base = X (alpha + beta = 1) or the
+        // accumulator; the rest component is then set so that the new phi equals
+        // sum(base) + gamma sum_k L_k (identical in exact arithmetic, since
+        // sum_k g_k = sum_k X_k = phi), which keeps FP32 rounding from drifting
+        // the conserved moment.
+        T o1[9], o2[9];
+        T sumL = T(0), sumB = T(0);
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             const T gk = wq<T>(k) * (ph + (T(ex(k)) * Px + T(ey(k)) * Py));
@@ -433,11 +441,30 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             // Eq. (21) with the outward normal of a unit cell
             const T L = -(T(ex(k)) * (fE[fidx] - fE[fidx - 1]) + T(ey(k)) * (fN[fidx] - fN[fidx - WF]));
             const T Xk = sX[k * NH + hidx];
-            T v = p.al1 * Xk + p.be1 * gk + p.ga1 * L;
-            if constexpr (KIND == KIND_T3B) v += static_cast<const T *>(p.acc)[k * plane + g];
-            if constexpr (KIND == KIND_T3A) p.out2[k * plane + g] = p.al2 * Xk + p.be2 * gk + p.ga2 * L;
-            o1[k] = v;
-            phn += v;
+            T base = Xk;
+            if constexpr (KIND == KIND_T3B) {
+                base = static_cast<const T *>(p.acc)[k * plane + g];
+                sumB += base;
+            }
+            o1[k] = base + p.be1 * (gk - Xk) + p.ga1 * L;
+            if constexpr (KIND == KIND_T3A) o2[k] = Xk + p.be2 * (gk - Xk) + p.ga2 * L;
+            sumL += L;
+        }
+        const T phn = (KIND == KIND_T3B ? sumB : ph) + p.ga1 * sumL;
+        {
+            T r = T(0);
+#pragma unroll
+            for (int k = 1; k < 9; k++) r += o1[k];
+            o1[0] = phn - r;
+        }
+        if constexpr (KIND == KIND_T3A) {
+            T r = T(0);
+#pragma unroll
+            for (int k = 1; k < 9; k++) r += o2[k];
+            o2[0] = (ph + p.ga2 * sumL) - r;
+            T *O2 = p.out2;
+#pragma unroll
+            for (int k = 0; k < 9; k++) O2[k * plane + g] = o2[k];
         }
         if constexpr (DEV) {
             __half *Oq = static_cast<__half *>(p.out1);
