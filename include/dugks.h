@@ -137,6 +137,32 @@ int dugks_load_state(dugks_ctx *c, const void *host, size_t bytes, int64_t step_
 /* Frees everything; NULL-safe; waits for the context's outstanding work. */
 void dugks_destroy(dugks_ctx *c);
 
+/* Allocation-free FP64 sum of a device field. The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc where they need a mass,
+ * such as code running while a stream is captured into a CUDA graph, hosts
+ * whose device memory is fully reserved by another allocator, and latency-
+ * critical loops that cannot take the implicit synchronisation of cudaMalloc.
+ * It runs the same reduction as dugks_mass_device (one FP64 partial per 32 x 8
+ * tile, then a fixed-order sum) with the partials in a static device array of
+ * DUGKS_NOALLOC_MAX_TILES doubles (512 KiB), which every GPU that loads the
+ * library holds until the process exits.
+ *   field    device pointer: ny rows of nx values, row stride pitch elements
+ *   dtype    0 = double, 1 = float
+ *   out_dev  device pointer to one double, written by the kernels
+ *   cuda_stream  cudaStream_t to launch on (NULL = legacy default stream)
+ * Returns DUGKS_EINVAL for bad arguments or when ceil(nx/32) * ceil(ny/8)
+ * exceeds DUGKS_NOALLOC_MAX_TILES (e.g. more than 4096 x 4096 cells), and
+ * DUGKS_ECUDA when the launch fails. It enqueues work and does not wait.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call on a device shares the array: calls whose kernels may overlap on
+ * the GPU (different streams without ordering) race and must be serialised by
+ * the caller. Each call overwrites the entries it reads, so no clearing is
+ * needed between calls. */
+#define DUGKS_NOALLOC_MAX_TILES 65536
+int dugks_field_mass_noalloc(const void *field, int dtype, int32_t nx, int32_t ny, int32_t pitch,
+                             double *out_dev, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

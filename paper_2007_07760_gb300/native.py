@@ -57,7 +57,10 @@ SIGNATURES = [
     ("dugks_save_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(_I64)]),
     ("dugks_load_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _I64]),
     ("dugks_destroy", None, [_VP]),
+    ("dugks_field_mass_noalloc", ctypes.c_int,
+     [_VP, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
 ]
+DUGKS_NOALLOC_MAX_TILES = 65536
 
 
 def lib_path() -> str:
@@ -174,6 +177,15 @@ def _buf(buf):
         return buf.ctypes.data, buf.nbytes
     # torch tensor (e.g. pinned host memory)
     return buf.data_ptr(), buf.numel() * buf.element_size()
+
+
+def dugks_field_mass_noalloc(field_ptr: int, dtype: int, nx: int, ny: int, pitch: int, out_ptr: int,
+                             stream: int | None = None) -> int:
+    """FP64 sum of a device field (double: dtype 0, float: dtype 1) into the
+    device double at out_ptr, without allocating device memory. Returns the
+    status code (enqueues only; does not wait)."""
+    return lib().dugks_field_mass_noalloc(ctypes.c_void_p(field_ptr), int(dtype), int(nx), int(ny), int(pitch),
+                                          ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream or 0))
 
 
 def make_params(nx, ny, W=4.0, M=0.01, cfl=0.8, order=2, flux=0, stages=2, precision="fp64",
