@@ -54,11 +54,10 @@ def kernel_source_hash() -> str:
 def workload(name: str, precision: str):
     if name == "slotted_disk256":
         prob = WL.slotted_disk256(order=3, flux=0, stages=2)
-    elif name == "vortex1024":
-        prob = WL.vortex1024(order=3, flux=0, stages=2)
-    elif name == "vortex4096":
-        prob = WL.vortex1024(order=3, flux=0, stages=2, n=4096)
-        prob.name = "vortex4096"
+    elif name.startswith("vortex"):
+        n = int(name[len("vortex"):] or 1024)
+        prob = WL.vortex1024(order=3, flux=0, stages=2, n=n)
+        prob.name = name
     elif name == "drop64":
         prob = WL.drop64()
     else:

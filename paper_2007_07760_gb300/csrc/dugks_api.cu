@@ -1,11 +1,15 @@
 // dugks_api.cu -- the C ABI of libdugks.so (declared in include/dugks.h).
 //
-// Host logic only: parameter checks, device memory of a context, the
-// per-step coefficients of the method, buffer rotation and error handling.
-// All arithmetic of the time step runs in the kernels of dugks_kernels.cuh.
+// Host logic only: parameter checks, the device memory of a context and its
+// plane layout (ghost border of GHOST cells), TMA tensor maps, the per-step
+// coefficients of the method, face-stencil coefficients, buffer rotation and
+// error handling. All arithmetic of the time step runs in the kernels.
+#include <cudaTypedefs.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -21,20 +25,26 @@ struct dugks_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int pitch = 0;
-    size_t plane = 0;           // ny * pitch elements
+    size_t plane = 0;           // (ny + 2 GHOST) * pitch elements
     size_t tsize = 8, ssize = 8;
     int nsets = 2, nphi = 2;
     void *X[3] = {nullptr, nullptr, nullptr};
     void *phi[3] = {nullptr, nullptr, nullptr};
     int cur = 0;                // current state set (two-stage)
-    int pr[3] = {0, 1, 2};      // phi plane roles (see step_*)
-    void *phi0 = nullptr;       // initial phi (T)
+    int pr[3] = {0, 1, 2};      // phi plane roles (see step_t2 / step_t3)
+    void *phi0 = nullptr;       // initial phi (T, plane layout)
     void *ufield = nullptr, *vfield = nullptr;
     void *tmp = nullptr;        // ny * nx T, phi readout
     double *partial = nullptr;  // per-tile FP64 mass partials (scratch)
     double *dmass = nullptr;    // one double
     int *dstatus = nullptr;     // sticky device flags
-    int ntiles = 0, tiles_x = 0;
+    int tile_w = TILE_X, tile_h = TILE_Y, tiles_x = 0, ntiles = 0;
+    // TMA-staged two-stage path (orders 2, 3)
+    bool fast = false;
+    int variant = 0;
+    CUtensorMap tmX[2], tmPhi[3];
+    double coef_h = -1.0;
+    std::vector<unsigned char> coefs;   // FaceCoefs<T> of the current h
     int vel_kind = DUGKS_VEL_UNIFORM;
     double vel[4] = {0, 0, 0, 0};
     bool initialized = false;
@@ -63,7 +73,7 @@ bool is_fp64(const dugks_ctx *c) { return c->p.precision == DUGKS_FP64; }
 int check_params(const dugks_params *p, std::string &why) {
     if (!p) { why = "params is NULL"; return DUGKS_EINVAL; }
     if (p->nx < 8 || p->ny < 8) { why = "nx and ny must be >= 8"; return DUGKS_EINVAL; }
-    if ((int64_t)p->nx * p->ny > (int64_t)1 << 31) { why = "grid too large"; return DUGKS_EINVAL; }
+    if ((int64_t)(p->nx + 2 * GHOST + 32) * (p->ny + 2 * GHOST) > (int64_t)1 << 31) { why = "grid too large"; return DUGKS_EINVAL; }
     if (!(p->W > 0) || !(p->M > 0)) { why = "W and M must be > 0"; return DUGKS_EINVAL; }
     if (!(p->cfl > 0) || p->cfl > 1.0) { why = "cfl must be in (0, 1]"; return DUGKS_EINVAL; }
     if (p->order < 2 || p->order > 4) { why = "order must be 2, 3 or 4"; return DUGKS_EINVAL; }
@@ -86,7 +96,11 @@ StepParams<T> base_params(const dugks_ctx *c) {
     q.nx = c->p.nx;
     q.ny = c->p.ny;
     q.pitch = c->pitch;
+    q.plane = c->plane;
+    q.status = c->dstatus;
     q.tiles_x = c->tiles_x;
+    q.tile_w = c->tile_w;
+    q.tile_h = c->tile_h;
     q.ufield = static_cast<const T *>(c->ufield);
     q.vfield = static_cast<const T *>(c->vfield);
     const double tau = 3.0 * c->p.M;
@@ -112,6 +126,125 @@ void face_coefs(StepParams<T> &q, double tau, double h) {
     q.c3 = (T)(tau * h / (2.0 * tau + h));
 }
 
+// ---- face stencils of the fast path ------------------------------------------
+// The face value bar f_k(x_b) is a fixed linear combination of bar f^+_k at the
+// cells around the face: the Taylor expansion of Eq. (26) (value + d.grad
+// + d d : H / 2 with the 9-point lattice-moment gradient and Hessian) about the
+// upwind cell, or the central form of Eq. (25). Weights at (a, b) of the
+// 3 x 3 block around the expansion cell:
+double G9x(int a, int b) { return a * (b == 0 ? 1.0 / 3.0 : 1.0 / 12.0); }
+double G9y(int a, int b) { return b * (a == 0 ? 1.0 / 3.0 : 1.0 / 12.0); }
+double H9(int i, int j, int a, int b) {   // i, j in {0: x, 1: y}
+    if (i != j) return (a != 0 && b != 0) ? 0.25 * a * b : 0.0;
+    const int along = i == 0 ? a : b, across = i == 0 ? b : a;
+    if (along == 0 && across == 0) return -4.0 / 3.0;
+    if (across == 0) return 2.0 / 3.0;
+    if (along == 0) return -1.0 / 3.0;
+    return 1.0 / 6.0;
+}
+double taylor_w(int order, double dx, double dy, int a, int b) {
+    double w = (a == 0 && b == 0) ? 1.0 : 0.0;
+    w += dx * G9x(a, b) + dy * G9y(a, b);
+    if (order >= 3)
+        w += 0.5 * dx * dx * H9(0, 0, a, b) + dx * dy * H9(0, 1, a, b) + 0.5 * dy * dy * H9(1, 1, a, b);
+    return w;
+}
+
+template <typename T>
+FaceCoefs<T> make_face_coefs(int order, int flux, double h) {
+    double e[9][3][4] = {}, n[9][4][4] = {};
+    for (int k = 0; k < 9; k++) {
+        const int kx = ex(k), ky = ey(k);
+        // east face: taps (b, a) -> e[k][b + 1][a + 1], b in -1..1, a in -1..2
+        auto addE = [&](int cx, double wgt, double dx, double dy) {   // expansion about cell (cx, 0)
+            for (int b = -1; b <= 1; b++)
+                for (int a = -1; a <= 1; a++) e[k][b + 1][cx + a + 1] += wgt * taylor_w(order, dx, dy, a, b);
+        };
+        auto addN = [&](int cy, double wgt, double dx, double dy) {   // expansion about cell (0, cy)
+            for (int b = -1; b <= 1; b++)
+                for (int a = -1; a <= 1; a++) n[k][cy + b + 1][a + 1] += wgt * taylor_w(order, dx, dy, a, b);
+        };
+        if (flux == DUGKS_UPWIND) {
+            if (kx > 0) addE(0, 1.0, 0.5 - h, -ky * h);
+            else if (kx < 0) addE(1, 1.0, h - 0.5, -ky * h);
+            else { addE(0, 0.5, 0.5, -ky * h); addE(1, 0.5, -0.5, -ky * h); }
+            if (ky > 0) addN(0, 1.0, -kx * h, 0.5 - h);
+            else if (ky < 0) addN(1, 1.0, -kx * h, h - 0.5);
+            else { addN(0, 0.5, -kx * h, 0.5); addN(1, 0.5, -kx * h, -0.5); }
+        } else {
+            // east: (F_c + F_E)/2 - h [xi_x (F_E - F_c) + xi_y (dF/dy(c) + dF/dy(E))/2]
+            e[k][1][1] += 0.5 + h * kx;
+            e[k][1][2] += 0.5 - h * kx;
+            n[k][1][1] += 0.5 + h * ky;
+            n[k][2][1] += 0.5 - h * ky;
+            for (int b = -1; b <= 1; b++)
+                for (int a = -1; a <= 1; a++) {
+                    e[k][b + 1][a + 1] += -0.5 * h * ky * G9y(a, b);
+                    e[k][b + 1][a + 2] += -0.5 * h * ky * G9y(a, b);
+                    n[k][b + 1][a + 1] += -0.5 * h * kx * G9x(a, b);
+                    n[k][b + 2][a + 1] += -0.5 * h * kx * G9x(a, b);
+                }
+        }
+    }
+    FaceCoefs<T> cf;
+    for (int k = 0; k < 9; k++) {
+        for (int b = 0; b < 3; b++)
+            for (int a = 0; a < 4; a++) cf.e[k][b][a] = (T)e[k][b][a];
+        for (int b = 0; b < 4; b++)
+            for (int a = 0; a < 4; a++) cf.n[k][b][a] = (T)n[k][b][a];
+    }
+    return cf;
+}
+
+// ---- TMA tensor maps -----------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+CUtensorMapDataType tma_type(size_t es, bool half) {
+    if (half) return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    return es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+}
+
+// planes of `es`-byte elements at base: dims (pitch, ny + 2G[, nplanes]), box (bw, bh[, nplanes])
+bool encode_map(CUtensorMap *m, void *base, size_t es, bool half, const dugks_ctx *c, int nplanes, int bw, int bh) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)(c->p.ny + 2 * GHOST), (cuuint64_t)nplanes};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * es, (cuuint64_t)c->plane * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)nplanes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t rank = nplanes > 1 ? 3 : 2;
+    CUresult r = fn(m, tma_type(es, half), rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+template <typename T, typename ST>
+bool setup_fast(dugks_ctx *c) {
+    const FastGeom g = Launch<T, ST>::fast_geom(c->variant);
+    const bool half = Store<T, ST>::deviation;
+    for (int s = 0; s < 2; s++)
+        if (!encode_map(&c->tmX[s], c->X[s], sizeof(ST), half, c, 9, g.box_w, g.box_h)) return false;
+    for (int s = 0; s < c->nphi; s++)
+        if (!encode_map(&c->tmPhi[s], c->phi[s], sizeof(T), false, c, 1, g.box_wt, g.box_h)) return false;
+    c->tile_w = g.tile_w;
+    c->tile_h = g.tile_h;
+    return true;
+}
+
 template <typename T, typename ST>
 int run_init(dugks_ctx *c) {
     StepParams<T> q = base_params<T>(c);
@@ -119,18 +252,12 @@ int run_init(dugks_ctx *c) {
     const double frac = c->p.stages == 2 ? 0.5 : 0.25;
     if (Store<T, ST>::deviation) {
         c->pr[0] = 0; c->pr[1] = 1; c->pr[2] = 2;
-        q.out1 = c->X[c->cur];
-        q.phi_out = static_cast<T *>(c->phi[c->pr[0]]);
-    } else {
-        q.out1 = c->X[c->cur];
     }
+    q.out1 = c->p.stages == 3 ? c->X[0] : c->X[c->cur];
+    // deviation storage: phi of the state; otherwise phi0 as the previous level
+    q.phi_out = static_cast<T *>(c->phi[c->pr[0]]);
     cudaError_t e = Launch<T, ST>::init(q, static_cast<const T *>(c->phi0), (T)(frac * c->p.cfl), c->p.order, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
-    if (!Store<T, ST>::deviation) {
-        // previous phi for d(phi u)/dt: phi0 (unused at the first step, where D = 0)
-        e = cudaMemcpyAsync(c->phi[c->pr[0]], c->phi0, c->plane * sizeof(T), cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "init copy");
-    }
     c->initialized = true;
     c->mass_valid = false;
     return DUGKS_OK;
@@ -145,10 +272,9 @@ int ensure_init(dugks_ctx *c) {
     }
 }
 
-// One two-stage step.  Non-deviation storage: X[cur] -> X[1-cur]; phi[pr0]
-// holds phi^{n-1} and receives nothing, phi[pr1] receives phi^n.
-// Deviation storage: phi[pr0] = phi^n (of X), phi[pr1] = phi^{n-1},
-// phi[pr2] receives phi^{n+1}.
+// One two-stage step. Full storage: X[cur] -> X[1-cur]; phi[pr0] holds
+// phi^{n-1}, phi[pr1] receives phi^n. Deviation storage: phi[pr0] = phi^n
+// (of X), phi[pr1] = phi^{n-1}, phi[pr2] receives phi^{n+1}.
 template <typename T, typename ST>
 int step_t2(dugks_ctx *c) {
     StepParams<T> q = base_params<T>(c);
@@ -158,7 +284,7 @@ int step_t2(dugks_ctx *c) {
     q.a = (T)a;
     q.b = (T)b;
     face_coefs(q, tau, h);
-    // tilde f^{n+1} = (4/3) bar f^+ - (1/3) tilde f + dt L
+    // tilde f^{n+1} = (4/3) bar f^+ - (1/3) tilde f + dt L = X + (4b/3)(g - X) + dt L
     q.al1 = (T)(4.0 / 3.0 * a - 1.0 / 3.0);
     q.be1 = (T)(4.0 / 3.0 * b);
     q.ga1 = (T)dt;
@@ -170,15 +296,35 @@ int step_t2(dugks_ctx *c) {
     q.X = c->X[c->cur];
     q.out1 = c->X[1 - c->cur];
     q.mass_partial = c->partial;
+    int iPc = 0, iPo, iOut;
     if (Store<T, ST>::deviation) {
-        q.phi_cur = static_cast<const T *>(c->phi[c->pr[0]]);
-        q.phi_old = static_cast<const T *>(c->phi[c->pr[1]]);
-        q.phi_out = static_cast<T *>(c->phi[c->pr[2]]);
+        iPc = c->pr[0]; iPo = c->pr[1]; iOut = c->pr[2];
+        q.phi_cur = static_cast<const T *>(c->phi[iPc]);
     } else {
-        q.phi_old = static_cast<const T *>(c->phi[c->pr[0]]);
-        q.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
+        iPo = c->pr[0]; iOut = c->pr[1];
     }
-    cudaError_t e = Launch<T, ST>::step(q, c->p.order, c->p.flux, KIND_T2, c->stream);
+    q.phi_old = static_cast<const T *>(c->phi[iPo]);
+    q.phi_out = static_cast<T *>(c->phi[iOut]);
+    cudaError_t e;
+    if (c->fast) {
+        if (c->coef_h != h) {
+            FaceCoefs<T> cf = make_face_coefs<T>(c->p.order, c->p.flux, h);
+            c->coefs.assign(reinterpret_cast<unsigned char *>(&cf), reinterpret_cast<unsigned char *>(&cf) + sizeof cf);
+            c->coef_h = h;
+        }
+        const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs.data());
+        FastExtra<T> fx{};
+        if (c->vel_kind == DUGKS_VEL_VORTEX) {   // reversal factor cos(pi t / T), in FP64
+            const double PI = 3.14159265358979323846, Tp = c->vel[2];
+            fx.vc_t = (T)std::cos(PI * t / Tp);
+            fx.vc_told = (T)std::cos(PI * (t - dt) / Tp);
+            fx.vc_tface = (T)std::cos(PI * (t + h) / Tp);
+        }
+        e = Launch<T, ST>::step_fast(q, cf, fx, c->tmX[c->cur], c->tmPhi[iPo], c->tmPhi[iPc], c->p.order,
+                                     c->p.flux, c->variant, c->stream);
+    } else {
+        e = Launch<T, ST>::step(q, c->p.order, c->p.flux, KIND_T2, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
     c->cur = 1 - c->cur;
     if (Store<T, ST>::deviation) {
@@ -314,19 +460,23 @@ void free_ctx(dugks_ctx *c) {
     delete c;
 }
 
-// host doubles (ny * nx) -> device T plane with pitch
+// host doubles (ny * nx, x fastest) -> device plane of T with the periodic ghost border
 int upload_plane(dugks_ctx *c, void *dst, const double *src) {
-    const int nx = c->p.nx, ny = c->p.ny;
+    const int nx = c->p.nx, ny = c->p.ny, G = GHOST;
+    const int rows = ny + 2 * G;
+    std::vector<double> pad((size_t)rows * c->pitch, 0.0);
+    for (int y = -G; y < ny + G; y++)
+        for (int x = -G; x < nx + G; x++) {
+            const int sx = ((x % nx) + nx) % nx, sy = ((y % ny) + ny) % ny;
+            pad[(size_t)(y + G) * c->pitch + (x + G)] = src[(size_t)sy * nx + sx];
+        }
     cudaError_t e;
     if (is_fp64(c)) {
-        e = cudaMemcpy2DAsync(dst, c->pitch * sizeof(double), src, nx * sizeof(double), nx * sizeof(double), ny,
-                              cudaMemcpyHostToDevice, c->stream);
+        e = cudaMemcpy(dst, pad.data(), pad.size() * sizeof(double), cudaMemcpyHostToDevice);
     } else {
-        std::vector<float> tmp((size_t)nx * ny);
-        for (size_t i = 0; i < tmp.size(); i++) tmp[i] = (float)src[i];
-        e = cudaMemcpy2DAsync(dst, c->pitch * sizeof(float), tmp.data(), nx * sizeof(float), nx * sizeof(float), ny,
-                              cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // tmp goes out of scope
+        std::vector<float> f(pad.size());
+        for (size_t i = 0; i < f.size(); i++) f[i] = (float)pad[i];
+        e = cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "upload");
     return DUGKS_OK;
@@ -362,8 +512,13 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     int r = check_params(p, why);
     if (r != DUGKS_OK) return r;
     if (!phi0_host) return DUGKS_EINVAL;
+    for (size_t i = 0; i < (size_t)p->nx * p->ny; i++)
+        if (!std::isfinite(phi0_host[i])) return DUGKS_ENONFINITE;
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DUGKS_ECUDA;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return DUGKS_ECUDA;
+    }
     dugks_ctx *c = new dugks_ctx();
     c->p = *p;
     cudaGetDevice(&c->dev);
@@ -378,12 +533,21 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     }
     c->tsize = is_fp64(c) ? 8 : 4;
     c->ssize = p->precision == DUGKS_FP64 ? 8 : p->precision == DUGKS_FP32 ? 4 : 2;
-    c->pitch = (p->nx + 31) / 32 * 32;
-    c->plane = (size_t)p->ny * c->pitch;
+    c->pitch = (p->nx + 2 * GHOST + 31) / 32 * 32;
+    c->plane = (size_t)(p->ny + 2 * GHOST) * c->pitch;
     c->nsets = p->stages == 3 ? 3 : 2;
     c->nphi = p->precision == DUGKS_FP16F ? 3 : 2;
-    c->tiles_x = (p->nx + TILE_X - 1) / TILE_X;
-    c->ntiles = c->tiles_x * ((p->ny + TILE_Y - 1) / TILE_Y);
+    // the TMA-staged kernel serves the two-stage scheme at orders 2 and 3
+    c->fast = p->stages == 2 && p->order <= 3 && encode_fn() != nullptr;
+    if (c->fast) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+        const FastGeom big = p->precision == DUGKS_FP64 ? Launch<double, double>::fast_geom(0)
+                             : p->precision == DUGKS_FP32 ? Launch<float, float>::fast_geom(0)
+                                                          : Launch<float, __half>::fast_geom(0);
+        const long tiles = (long)((p->nx + big.tile_w - 1) / big.tile_w) * ((p->ny + big.tile_h - 1) / big.tile_h);
+        c->variant = tiles >= 2L * sms ? 0 : 1;   // small grids: smaller tiles to fill the SMs
+    }
     bool ok = true;
     for (int s = 0; s < c->nsets && ok; s++) {
         // the three-stage accumulator (set 2) is always in the arithmetic type
@@ -393,28 +557,36 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     for (int s = 0; s < c->nphi && ok; s++) ok = cudaMalloc(&c->phi[s], c->plane * c->tsize) == cudaSuccess;
     if (ok) ok = cudaMalloc(&c->phi0, c->plane * c->tsize) == cudaSuccess;
     if (ok) ok = cudaMalloc(&c->tmp, (size_t)p->nx * p->ny * c->tsize) == cudaSuccess;
-    if (ok) ok = cudaMalloc(&c->partial, (size_t)c->ntiles * sizeof(double)) == cudaSuccess;
     if (ok) ok = cudaMalloc(&c->dmass, sizeof(double)) == cudaSuccess;
     if (ok) ok = cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
+    if (ok && c->fast) {
+        bool enc = p->precision == DUGKS_FP64 ? setup_fast<double, double>(c)
+                   : p->precision == DUGKS_FP32 ? setup_fast<float, float>(c)
+                                                : setup_fast<float, __half>(c);
+        if (!enc) {   // use the generic CUDA kernel instead
+            c->fast = false;
+            c->tile_w = TILE_X;
+            c->tile_h = TILE_Y;
+        }
+    }
+    c->tiles_x = (p->nx + c->tile_w - 1) / c->tile_w;
+    c->ntiles = c->tiles_x * ((p->ny + c->tile_h - 1) / c->tile_h);
+    if (ok) ok = cudaMalloc(&c->partial, (size_t)c->ntiles * sizeof(double)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_ctx(c);
         return DUGKS_ENOMEM;
     }
     cudaError_t e = cudaMemsetAsync(c->dstatus, 0, sizeof(int), c->stream);
-    // zero the pitch padding so raw checkpoints are deterministic
+    // zero everything so raw checkpoints and the pitch padding are deterministic
     for (int s = 0; s < c->nsets && e == cudaSuccess; s++)
         e = cudaMemsetAsync(c->X[s], 0, 9 * c->plane * ((p->stages == 3) ? c->tsize : c->ssize), c->stream);
     for (int s = 0; s < c->nphi && e == cudaSuccess; s++) e = cudaMemsetAsync(c->phi[s], 0, c->plane * c->tsize, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         free_ctx(c);
         return DUGKS_ECUDA;
     }
-    for (size_t i = 0; i < (size_t)p->nx * p->ny; i++)
-        if (!std::isfinite(phi0_host[i])) {
-            free_ctx(c);
-            return DUGKS_ENONFINITE;
-        }
     r = upload_plane(c, c->phi0, phi0_host);
     if (r == DUGKS_OK) r = sync_ctx(c);
     if (r != DUGKS_OK) {
@@ -444,6 +616,10 @@ int dugks_set_velocity(dugks_ctx *c, int kind, const double *params, const doubl
         break;
     case DUGKS_VEL_FIELD: {
         if (!u_host || !v_host) return fail(c, DUGKS_EINVAL, "field velocity needs u and v arrays");
+        for (size_t i = 0; i < (size_t)c->p.nx * c->p.ny; i++)
+            if (!std::isfinite(u_host[i]) || !std::isfinite(v_host[i]))
+                return fail(c, DUGKS_EINVAL, "velocity field must be finite");
+        cudaStreamSynchronize(c->stream);   // the field may be in use by queued steps
         if (!c->ufield) {
             if (cudaMalloc(&c->ufield, c->plane * c->tsize) != cudaSuccess ||
                 cudaMalloc(&c->vfield, c->plane * c->tsize) != cudaSuccess) {
@@ -534,6 +710,7 @@ int dugks_status(dugks_ctx *c) {
     int flags = 0;
     cudaError_t e = cudaMemcpy(&flags, c->dstatus, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "read status");
+    if (flags & 2) return fail(c, DUGKS_ETIMEOUT, "a device wait ran out");
     if (flags & 1) return fail(c, DUGKS_ENONFINITE, "the field holds NaN or Inf");
     return DUGKS_OK;
 }

@@ -1,0 +1,533 @@
+// dugks_fast.cuh -- the two-stage DUGKS step for stencil orders 2 and 3, staged
+// by TMA (sm_103a).
+//
+// Same arithmetic as step_kernel (dugks_kernels.cuh), organised for throughput:
+//  * the tile's 9 distribution planes plus a 3-cell halo arrive in shared
+//    memory as ONE 3D TMA box (the ghost border of the plane layout makes every
+//    halo a plain rectangle), the older phi plane as a 2D box; one mbarrier;
+//  * the loop over the 9 velocities is outermost (and not unrolled, to keep the
+//    kernel small enough for the instruction cache): per direction k,
+//    bar f^+_k on the tile + 2 cells, then bar f_k at the east and north faces
+//    of every face-owner cell as fixed 12-tap linear stencils of bar f^+_k
+//    (coefficients depend only on k and h: computed on the host);
+//  * the flux of Eq. (21) is split as
+//      L_k = -[(1 - c2) Dbar_k + c2 w_k Phi_k + c3 w_k Psi_k]
+//    with Dbar_k the face-difference of bar f_k, Phi_k that of
+//    f^eq_b / w_k = phi_b + 3 xi_k.(phi_b u_b) and Psi_k that of xi_k.V_b.
+//    During the direction loop each cell's X_k + beta (g_k - X_k) + gamma L_k
+//    minus its phi_b part is written over X_k in the TMA buffer (dead by then);
+//    once phi_b is known, a second loop adds the phi_b part and stores.
+// Thread layout: a warp owns 32 consecutive face-owner columns (lane l is column
+// l - 1) and MR consecutive rows; the CTA's face owners are 32 x (NW * MR), its
+// cells TX = 31 by TY = NW * MR - 1.
+#pragma once
+
+#include <cuda.h>
+
+#include "dugks_kernels.cuh"
+
+namespace dugks {
+
+// Face stencils of one reconstruction time h: east face of cell c over rows
+// -1..1 and columns -1..2 around c, north face over rows -1..2, columns -1..1
+// (stored with a zero fourth column).
+template <typename T>
+struct FaceCoefs {
+    T e[9][3][4];
+    T n[9][4][4];
+};
+
+// Per-step scalars of the fast kernel that the generic parameters do not carry.
+template <typename T>
+struct FastExtra {
+    T vc_t, vc_told, vc_tface;   // vortex reversal factors cos(pi t / T) at t, t_old, t_face
+};
+
+// ---- TMA and mbarrier (inline PTX) -------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait: gives up after max_iter polls (each poll may suspend briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, uint32_t max_iter) {
+    for (uint32_t i = 0; i < max_iter; i++)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr uint32_t MBAR_MAX_POLLS = 1u << 22;
+
+// wrap a tile-relative index into [0, n) (at most a few periods away)
+__device__ __forceinline__ int wrap_small(int i, int n) {
+    while (i < 0) i += n;
+    while (i >= n) i -= n;
+    return i;
+}
+
+// periodic images of one value inside the ghost border (cells near an edge only)
+template <typename T, typename V>
+__device__ __noinline__ void put_ghosts(const StepParams<T> &p, V *plane, int x, int y, V v) {
+#pragma unroll 1
+    for (int ay = -1; ay <= 1; ay++) {
+        const int yy = y + ay * p.ny;
+        if (yy < -GHOST || yy >= p.ny + GHOST) continue;
+#pragma unroll 1
+        for (int ax = -1; ax <= 1; ax++) {
+            const int xx = x + ax * p.nx;
+            if ((ax == 0 && ay == 0) || xx < -GHOST || xx >= p.nx + GHOST) continue;
+            plane[gidx(p, xx, yy)] = v;
+        }
+    }
+}
+
+template <typename T, typename ST, int NW, int MR>
+struct FastTile {
+    static constexpr int NT = NW * 32;
+    static constexpr int TX = 31, TY = NW * MR - 1;         // cells written
+    static constexpr int RW = TX + 6, RH = TY + 6;          // state region: halo 3
+    static constexpr int CW = TX + 4, CH = TY + 4;          // cell-quantity region: halo 2
+    static constexpr int NC = CW * CH;
+    // cell-quantity cells not owned by a thread: columns -2, TX, TX + 1 (all rows)
+    // and rows -2, TY, TY + 1 (columns -1 .. TX - 1)
+    static constexpr int NE = 3 * CH + 3 * 32;
+    static constexpr int NXS = (NE + NT - 1) / NT;          // extra slots per thread
+    static constexpr int AS = 16 / (int)sizeof(ST);         // TMA x alignment of the state (elements)
+    static constexpr int AT = 16 / (int)sizeof(T);          // ... of the phi planes
+    static constexpr int BW = (RW + AS - 1 + AS - 1) / AS * AS;   // state box width
+    static constexpr int BWT = (RW + AT - 1 + AT - 1) / AT * AT;  // phi box width
+    static constexpr bool DEV = Store<T, ST>::deviation;
+    // shared-memory carve-up (byte offsets, 128-B aligned TMA destinations first)
+    static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
+    static constexpr size_t oX = 0;
+    static constexpr size_t oPo = al(oX + sizeof(ST) * 9 * BW * RH);
+    static constexpr size_t oPc = al(oPo + sizeof(T) * BWT * RH);
+    static constexpr size_t oPhi = al(oPc + (DEV ? sizeof(T) * BWT * RH : 0));
+    static constexpr size_t oPart = al(oPhi + (DEV ? 0 : sizeof(T) * RW * RH));
+    static constexpr size_t oV = al(oPart + (DEV ? sizeof(T) * 9 * 32 * (TY + 1) : 0));
+    static constexpr size_t oF = al(oV + sizeof(T) * 2 * NC);
+    static constexpr size_t oNB = al(oF + sizeof(T) * 2 * NC);
+    static constexpr size_t oQ = al(oNB + sizeof(T) * 2 * NW * 32);
+    static constexpr size_t oCoef = al(oQ + sizeof(T) * 3 * NW * 32);
+    static constexpr size_t oVel = al(oCoef + sizeof(T) * (9 * 12 + 9 * 16 + 9 * 4));
+    static constexpr size_t oRed = al(oVel + sizeof(T) * 4 * (CW + CH));
+    static constexpr size_t oBar = oRed + sizeof(double) * 32;
+    static constexpr size_t smem_bytes = oBar + 16;
+    static constexpr uint32_t tx_bytes =
+        (uint32_t)(sizeof(ST) * 9 * BW * RH + sizeof(T) * BWT * RH * (DEV ? 2 : 1));
+};
+
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
+__global__ void __launch_bounds__(NW * 32)
+step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant__ FaceCoefs<T> cf,
+                 const __grid_constant__ FastExtra<T> fe_, const __grid_constant__ CUtensorMap tmX,
+                 const __grid_constant__ CUtensorMap tmPo, const __grid_constant__ CUtensorMap tmPc) {
+    using FT = FastTile<T, ST, NW, MR>;
+    constexpr int TX = FT::TX, TY = FT::TY, RW = FT::RW, CW = FT::CW, CH = FT::CH, NC = FT::NC;
+    constexpr int NT = FT::NT, BW = FT::BW, BWT = FT::BWT, RH = FT::RH, NE = FT::NE, NXS = FT::NXS;
+    constexpr bool DEV = FT::DEV;
+    static_assert(ORDER == 2 || ORDER == 3, "fast path covers orders 2 and 3");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    ST *sX = reinterpret_cast<ST *>(smem + FT::oX);
+    T *sPo = reinterpret_cast<T *>(smem + FT::oPo);
+    T *sPc = reinterpret_cast<T *>(smem + FT::oPc);
+    T *sPhi = reinterpret_cast<T *>(smem + FT::oPhi);
+    T *sPart = reinterpret_cast<T *>(smem + FT::oPart);
+    T *sV = reinterpret_cast<T *>(smem + FT::oV);
+    T *sF = reinterpret_cast<T *>(smem + FT::oF);
+    T *sNB = reinterpret_cast<T *>(smem + FT::oNB);
+    T *sQ = reinterpret_cast<T *>(smem + FT::oQ);
+    T *sCE = reinterpret_cast<T *>(smem + FT::oCoef);   // [9][3][4]
+    T *sCN = sCE + 9 * 12;                              // [9][4][4]
+    T *sK = sCN + 9 * 16;                               // [9][4]: xi_x, xi_y, w, 0
+    T *sVel = reinterpret_cast<T *>(smem + FT::oVel);   // vortex factors, see below
+    double *sred = reinterpret_cast<double *>(smem + FT::oRed);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + FT::oBar);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nx = p.nx, ny = p.ny;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    // padded-plane coordinates of the state box; ox = offset of relative x = -3 in the box
+    const int xs_raw = x0 - 3 + GHOST, ys = y0 - 3 + GHOST;
+    const int xs = xs_raw / FT::AS * FT::AS, ox = xs_raw - xs;
+    const int xst = xs_raw / FT::AT * FT::AT, oxt = xs_raw - xst;
+
+    // ---- S0: one TMA box for the 9 planes (+ phi planes) --------------------
+    if (tid == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(bar, FT::tx_bytes);
+        tma_load_3d(sX, &tmX, xs, ys, 0, bar);
+        tma_load_2d(sPo, &tmPo, xst, ys, bar);
+        if constexpr (DEV) tma_load_2d(sPc, &tmPc, xst, ys, bar);
+    }
+    // while the copy is in flight: tables of face coefficients, lattice, velocity
+    for (int i = tid; i < 9 * 12; i += NT) sCE[i] = (&cf.e[0][0][0])[i];
+    for (int i = tid; i < 9 * 16; i += NT) sCN[i] = (&cf.n[0][0][0])[i];
+    if (tid < 9) {
+        sK[tid * 4 + 0] = T(ex(tid));
+        sK[tid * 4 + 1] = T(ey(tid));
+        sK[tid * 4 + 2] = wq<T>(tid);
+        sK[tid * 4 + 3] = T(0);
+    }
+    // single vortex u = -U A(x) B(y) c(t), v = U A(y) B(x) c(t), with
+    // A(s) = sin^2(pi s / L), B(s) = sin(2 pi s / L) at cell centres (s = i + 1/2)
+    // and at faces (s = i + 1) of the wrapped cells of this tile (+2 halo)
+    T *sAxc = sVel, *sBxc = sAxc + CW, *sAxf = sBxc + CW, *sBxf = sAxf + CW;
+    T *sAyc = sBxf + CW, *sByc = sAyc + CH, *sAyf = sByc + CH, *sByf = sAyf + CH;
+    if (p.vel_kind == VEL_VORTEX) {
+        const T L = p.vp0;
+        for (int i = tid; i < 2 * (CW + CH); i += NT) {
+            const bool isx = i < 2 * CW;
+            const int j = isx ? (i >> 1) : ((i - 2 * CW) >> 1);
+            const bool face = (i & 1) != 0;
+            const int g = isx ? wrap_small(x0 + j - 2, nx) : wrap_small(y0 + j - 2, ny);
+            const T s = T(g) + (face ? T(1) : T(0.5));
+            const T sn = sinpi_(s / L);
+            const T A = sn * sn, B = sinpi_(T(2) * s / L);
+            if (isx) {
+                (face ? sAxf : sAxc)[j] = A;
+                (face ? sBxf : sBxc)[j] = B;
+            } else {
+                (face ? sAyf : sAyc)[j] = A;
+                (face ? sByf : sByc)[j] = B;
+            }
+        }
+    }
+    if (!mbar_wait_bounded(bar, 0, MBAR_MAX_POLLS)) {
+        // the copy never completed: flag it, give it one more bounded chance to
+        // land (it targets this CTA's shared memory), and leave
+        if (tid == 0) atomicOr(p.status, 2);
+        mbar_wait_bounded(bar, 0, MBAR_MAX_POLLS);
+        return;
+    }
+
+    // accessors (relative cell coordinates x, y of the tile)
+    auto xidx = [&](int x, int y) { return (y + 3) * BW + (x + 3 + ox); };   // + k * RH * BW
+    auto Xat = [&](int k, int x, int y) -> T {
+        const ST v = sX[k * RH * BW + xidx(x, y)];
+        if constexpr (DEV) {
+            const T ph = sPc[(y + 3) * BWT + (x + 3 + oxt)];
+            return sK[k * 4 + 2] * (ph + to_f(v) * p.qinv);
+        } else {
+            return (T)v;
+        }
+    };
+    auto PHI = [&](int x, int y) -> T {
+        if constexpr (DEV) return sPc[(y + 3) * BWT + (x + 3 + oxt)];
+        else return sPhi[(y + 3) * RW + (x + 3)];
+    };
+    // velocity of a cell centre (where = 0), east face (1) or north face (2)
+    auto vel = [&](int x, int y, int where, T t, T vc, T &u, T &v) {
+        if (p.vel_kind == VEL_UNIFORM) {
+            u = p.vp0;
+            v = p.vp1;
+        } else if (p.vel_kind == VEL_VORTEX) {
+            const int i = x + 2, j = y + 2;
+            const T Ax = where == 1 ? sAxf[i] : sAxc[i], Bx = where == 1 ? sBxf[i] : sBxc[i];
+            const T Ay = where == 2 ? sAyf[j] : sAyc[j], By = where == 2 ? sByf[j] : sByc[j];
+            u = -p.vp1 * Ax * By * vc;
+            v = p.vp1 * Ay * Bx * vc;
+        } else {
+            const int gx = wrap_small(x0 + x, nx), gy = wrap_small(y0 + y, ny);
+            if (where == 0) vel_cell(p, gx, gy, t, u, v);
+            else vel_face(p, gx, gy, where - 1, t, u, v);
+        }
+    };
+    // cell quantities of cell (x, y): phi, P = 3 phi u + tau V (g_k = w_k (phi + xi_k.P)),
+    // and V = theta n + 3 D into shared memory (face sources)
+    auto cell_q = [&](int x, int y, T &ph, T &Px, T &Py) {
+        ph = PHI(x, y);
+        const T ne = PHI(x + 1, y + 1), nw = PHI(x - 1, y + 1), se = PHI(x + 1, y - 1), sw = PHI(x - 1, y - 1);
+        const T gxp = (PHI(x + 1, y) - PHI(x - 1, y)) * T(1.0 / 3.0) + ((ne - nw) + (se - sw)) * T(1.0 / 12.0);
+        const T gyp = (PHI(x, y + 1) - PHI(x, y - 1)) * T(1.0 / 3.0) + ((ne - se) + (nw - sw)) * T(1.0 / 12.0);
+        const T g2 = gxp * gxp + gyp * gyp;
+        T nxv = T(0), nyv = T(0);
+        if (g2 > T(1e-24)) {  // Eq. (2); n = 0 where grad phi vanishes
+            const T inv = T(1) / sqrt(g2);
+            nxv = gxp * inv;
+            nyv = gyp * inv;
+        }
+        const T theta = p.theta_c * (ph - p.phiA) * (ph - p.phiB);  // Eq. (4)
+        T u, v;
+        vel(x, y, 0, p.t, fe_.vc_t, u, v);
+        T Dx = T(0), Dy = T(0);
+        if (p.useD) {  // d(phi u)/dt, backward difference
+            T uo, vo;
+            vel(x, y, 0, p.t_old, fe_.vc_told, uo, vo);
+            const T po = sPo[(y + 3) * BWT + (x + 3 + oxt)];
+            Dx = (ph * u - po * uo) * p.inv_dtD;
+            Dy = (ph * v - po * vo) * p.inv_dtD;
+        }
+        const T Vx = theta * nxv + T(3) * Dx, Vy = theta * nyv + T(3) * Dy;  // Eq. (14b)
+        Px = T(3) * ph * u + p.tau * Vx;
+        Py = T(3) * ph * v + p.tau * Vy;
+        const int j = (y + 2) * CW + (x + 2);
+        sV[j] = Vx;
+        sV[NC + j] = Vy;
+    };
+
+    // ---- S1: phi = sum_k X_k on the state region (Eq. (30)) ------------------
+    if constexpr (!DEV) {
+        for (int idx = tid; idx < RW * RH; idx += NT) {
+            const int y = idx / RW - 3, x = idx - (y + 3) * RW - 3;
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < 9; k++) s += (T)sX[k * RH * BW + xidx(x, y)];
+            sPhi[idx] = s;
+        }
+    }
+    __syncthreads();
+
+    // ---- S2: cell quantities: my MR cells and up to NXS halo cells ----------
+    const int fx = lane - 1;                // face-owner column
+    const int fy0 = warp * MR - 1;          // first face-owner row of this thread
+    T cg[MR], cPx[MR], cPy[MR];
+#pragma unroll
+    for (int r = 0; r < MR; r++) cell_q(fx, fy0 + r, cg[r], cPx[r], cPy[r]);
+    int exj[NXS], exx[NXS], exy[NXS];
+    T eg[NXS], ePx[NXS], ePy[NXS];
+#pragma unroll
+    for (int s = 0; s < NXS; s++) {
+        const int e = tid + s * NT;
+        exj[s] = -1;
+        exx[s] = exy[s] = 0;
+        eg[s] = ePx[s] = ePy[s] = T(0);
+        if (e < NE) {
+            int x, y;
+            if (e < 3 * CH) {
+                const int c = e / CH;
+                x = c == 0 ? -2 : TX + c - 1;
+                y = e - c * CH - 2;
+            } else {
+                const int e2 = e - 3 * CH, c = e2 >> 5;
+                y = c == 0 ? -2 : TY + c - 1;
+                x = (e2 & 31) - 1;
+            }
+            exx[s] = x;
+            exy[s] = y;
+            exj[s] = (y + 2) * CW + (x + 2);
+            cell_q(x, y, eg[s], ePx[s], ePy[s]);
+        }
+    }
+
+    // ---- S3: directions ------------------------------------------------------
+    T phbE[MR], phbN[MR], sumD[MR];
+#pragma unroll
+    for (int r = 0; r < MR; r++) phbE[r] = phbN[r] = sumD[r] = T(0);
+    const T gmc = p.ga1 * (T(1) - p.c2);    // gamma (1 - c2)
+    T fn0Prev = T(0), eyPrev = T(0);        // pending south difference of my first row
+    const int fbase = (fy0 + 2) * CW + (fx + 2);     // my first cell in the cell-quantity region
+    const int xbase = xidx(fx, fy0);                 // ... in the state box
+
+    // partial update of my cell r, direction k: X + beta (g - X) - gamma (1 - c2) Dbar
+    auto part_ref = [&](int k, int r) -> T & {
+        if constexpr (DEV) return sPart[(k * (TY + 1) + (fy0 + 1 + r)) * 32 + lane];
+        else return reinterpret_cast<T *>(sX)[k * RH * BW + xbase + r * BW];
+    };
+
+#pragma unroll 1
+    for (int k = 0; k < 9; k++) {
+        T *F = sF + (k & 1) * NC;
+        const T exk = sK[k * 4 + 0], eyk = sK[k * 4 + 1], wk = sK[k * 4 + 2];
+        // S3a: bar f^+_k = X_k + b (g_k - X_k) (increment form; a + b = 1)
+        T xk[MR], gk[MR];
+#pragma unroll
+        for (int r = 0; r < MR; r++) {
+            xk[r] = Xat(k, fx, fy0 + r);
+            gk[r] = wk * (cg[r] + (exk * cPx[r] + eyk * cPy[r]));
+            F[fbase + r * CW] = xk[r] + p.b * (gk[r] - xk[r]);
+        }
+#pragma unroll
+        for (int s = 0; s < NXS; s++) {
+            if (exj[s] >= 0) {
+                const T xe = Xat(k, exx[s], exy[s]);
+                const T ge = wk * (eg[s] + (exk * ePx[s] + eyk * ePy[s]));
+                F[exj[s]] = xe + p.b * (ge - xe);
+            }
+        }
+        __syncthreads();
+        // finish the previous direction's first-row partial with its south difference
+        if (k > 1 && fx >= 0 && fy0 >= 0) {
+            const T below = sNB[((k - 1) & 1) * NW * 32 + (warp - 1) * 32 + lane];
+            const T d = eyPrev * (fn0Prev - below);
+            part_ref(k - 1, 0) -= gmc * d;
+            sumD[0] += d;
+        }
+        // S3b: face values of my MR cells from a (MR + 3) x 4 window of bar f^+_k
+        T win[MR + 3][4];
+#pragma unroll
+        for (int i = 0; i < MR + 3; i++)
+#pragma unroll
+            for (int a = 0; a < 4; a++) win[i][a] = F[fbase + (i - 1) * CW + (a - 1)];
+        T cE[3][4], cN[4][3];
+#pragma unroll
+        for (int b = 0; b < 3; b++)
+#pragma unroll
+            for (int a = 0; a < 4; a++) cE[b][a] = sCE[(k * 3 + b) * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+#pragma unroll
+            for (int a = 0; a < 3; a++) cN[b][a] = sCN[(k * 4 + b) * 4 + a];
+        T fe[MR], fn[MR];
+#pragma unroll
+        for (int r = 0; r < MR; r++) {
+            T se = T(0), sn = T(0);
+#pragma unroll
+            for (int b = 0; b < 3; b++)
+#pragma unroll
+                for (int a = 0; a < 4; a++) se += cE[b][a] * win[r + b][a];
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+#pragma unroll
+                for (int a = 0; a < 3; a++) sn += cN[b][a] * win[r + b][a];
+            fe[r] = se;
+            fn[r] = sn;
+            phbE[r] += se;
+            phbN[r] += sn;
+        }
+        // Dbar_k = xi_x (f_E(c) - f_E(c - E)) + xi_y (f_N(c) - f_N(c - N)); partial update
+        // (direction 0 has xi = 0 and is completed from phi in S4)
+#pragma unroll
+        for (int r = 0; r < MR; r++) {
+            const T left = __shfl_up_sync(0xffffffffu, fe[r], 1);
+            T d = exk * (fe[r] - left);
+            if (r > 0) d += eyk * (fn[r] - fn[r - 1]);
+            if (k > 0 && fx >= 0 && fy0 + r >= 0) {
+                part_ref(k, r) = xk[r] + p.be1 * (gk[r] - xk[r]) - gmc * d;
+                sumD[r] += d;
+            }
+        }
+        fn0Prev = fn[0];
+        eyPrev = eyk;
+        sNB[(k & 1) * NW * 32 + warp * 32 + lane] = fn[MR - 1];
+    }
+    __syncthreads();
+    if (fx >= 0 && fy0 >= 0) {
+        const T below = sNB[(8 & 1) * NW * 32 + (warp - 1) * 32 + lane];
+        const T d = eyPrev * (fn0Prev - below);
+        part_ref(8, 0) -= gmc * d;
+        sumD[0] += d;
+    }
+
+    // ---- S4: face scalars, flux completion and store -------------------------
+    T qE[MR][3], qN[MR][3];
+#pragma unroll
+    for (int r = 0; r < MR; r++) {
+        T u, v;
+        vel(fx, fy0 + r, 1, p.t_face, fe_.vc_tface, u, v);
+        qE[r][0] = phbE[r];
+        qE[r][1] = phbE[r] * u;
+        qE[r][2] = phbE[r] * v;
+        vel(fx, fy0 + r, 2, p.t_face, fe_.vc_tface, u, v);
+        qN[r][0] = phbN[r];
+        qN[r][1] = phbN[r] * u;
+        qN[r][2] = phbN[r] * v;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) sQ[c * NW * 32 + warp * 32 + lane] = qN[MR - 1][c];
+    __syncthreads();
+
+    double msum = 0.0;
+    const size_t plane = p.plane;
+    const T ga = p.ga1, gc2 = p.ga1 * p.c2, gc3 = p.ga1 * p.c3;
+#pragma unroll
+    for (int r = 0; r < MR; r++) {
+        const int x = fx, y = fy0 + r;
+        // east differences from the lane to the west, north from the row below
+        T dE[3], dN[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            dE[c] = qE[r][c] - __shfl_up_sync(0xffffffffu, qE[r][c], 1);
+            const T below = r > 0 ? qN[r - 1][c] : (warp > 0 ? sQ[c * NW * 32 + (warp - 1) * 32 + lane] : T(0));
+            dN[c] = qN[r][c] - below;
+        }
+        const int gx = x0 + x, gy = y0 + y;
+        if (x < 0 || y < 0 || gx >= nx || gy >= ny) continue;
+        const int cj = fbase + r * CW;
+        // Delta V_b = (V(c + E) - V(c - E)) / 2 and likewise north
+        const T dVEx = T(0.5) * (sV[cj + 1] - sV[cj - 1]), dVEy = T(0.5) * (sV[NC + cj + 1] - sV[NC + cj - 1]);
+        const T dVNx = T(0.5) * (sV[cj + CW] - sV[cj - CW]), dVNy = T(0.5) * (sV[NC + cj + CW] - sV[NC + cj - CW]);
+        // gamma w_k (c2 Phi_k + c3 Psi_k) = w_k (xi_x A1 + xi_y A2 + xi_x^2 B1 + xi_x xi_y B2 + xi_y^2 B3)
+        const T A1 = gc2 * dE[0], A2 = gc2 * dN[0];
+        const T B1 = T(3) * gc2 * dE[1] + gc3 * dVEx;
+        const T B2 = T(3) * gc2 * (dE[2] + dN[1]) + gc3 * (dVEy + dVNx);
+        const T B3 = T(3) * gc2 * dN[2] + gc3 * dVNy;
+        // new phi = phi + gamma sum_k L_k (sum_k w_k xi_k = 0, sum_k w_k xi_a xi_b = delta_ab / 3)
+        const T phn = cg[r] - gmc * sumD[r] - (B1 + B3) * T(1.0 / 3.0);
+        const bool edge = gx < GHOST || gx >= nx - GHOST || gy < GHOST || gy >= ny - GHOST;
+        const size_t g = gidx(p, gx, gy);
+        T o[9];
+        const T S13 = B1 + B3;
+        o[1] = part_ref(1, r) - wq<T>(1) * (A1 + B1);
+        o[5] = part_ref(5, r) - wq<T>(5) * (B1 - A1);
+        o[3] = part_ref(3, r) - wq<T>(3) * (A2 + B3);
+        o[7] = part_ref(7, r) - wq<T>(7) * (B3 - A2);
+        o[2] = part_ref(2, r) - wq<T>(2) * ((A1 + A2) + (S13 + B2));
+        o[4] = part_ref(4, r) - wq<T>(4) * ((A2 - A1) + (S13 - B2));
+        o[6] = part_ref(6, r) - wq<T>(6) * ((S13 + B2) - (A1 + A2));
+        o[8] = part_ref(8, r) - wq<T>(8) * ((A1 - A2) + (S13 - B2));
+        // rest component: the new phi is exactly phn (up to this subtraction)
+        T rsum = T(0);
+#pragma unroll
+        for (int k = 1; k < 9; k++) rsum += o[k];
+        o[0] = phn - rsum;
+        if constexpr (DEV) {
+            __half *Oq = static_cast<__half *>(p.out1);
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const __half qv = __float2half_rn((o[k] - wq<T>(k) * phn) * (p.qscale / wq<T>(k)));
+                Oq[k * plane + g] = qv;
+                if (edge) put_ghosts(p, Oq + k * plane, gx, gy, qv);
+            }
+            p.phi_out[g] = phn;
+            if (edge) put_ghosts(p, p.phi_out, gx, gy, phn);
+        } else {
+            T *O = static_cast<T *>(p.out1);
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                O[k * plane + g] = o[k];
+                if (edge) put_ghosts(p, O + k * plane, gx, gy, o[k]);
+            }
+            p.phi_out[g] = cg[r];
+            if (edge) put_ghosts(p, p.phi_out, gx, gy, cg[r]);
+        }
+        msum += (double)phn;
+    }
+    if (p.mass_partial != nullptr) {
+        const double s = block_sum(msum, sred);
+        if (tid == 0) p.mass_partial[blockIdx.y * p.tiles_x + blockIdx.x] = s;
+    }
+}
+
+}  // namespace dugks

@@ -2,25 +2,37 @@
 // and the per-precision kernel instantiations (dugks_inst_*.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "dugks_fast.cuh"
 #include "dugks_kernels.cuh"
 
 namespace dugks {
 
-// Tile of one CTA of the fused step kernel.
+// Tile of one CTA of the generic fused step kernel.
 constexpr int TILE_X = 32;
 constexpr int TILE_Y = 8;
 constexpr int STEP_THREADS = 256;
 
-// Precision tags: 0 = FP64, 1 = FP32, 2 = FP32 arithmetic with FP16 deviation storage.
+// Geometry of a TMA-staged (fast) variant: 0 = 8 warps per CTA, 1 = 4 warps.
+struct FastGeom {
+    int threads, tile_w, tile_h;   // cells written per CTA
+    int box_w, box_h;              // state box (elements, rows)
+    int box_wt;                    // phi box width (elements)
+};
+
 template <typename T, typename ST>
 struct Launch {
     static cudaError_t step(const StepParams<T> &p, int order, int flux, int kind, cudaStream_t s);
     static cudaError_t init(const StepParams<T> &p, const T *phi0, T frac_dt, int order, cudaStream_t s);
     static cudaError_t mass_partial(const StepParams<T> &p, cudaStream_t s);
     static cudaError_t phi(const StepParams<T> &p, T *out, cudaStream_t s);
+    static FastGeom fast_geom(int variant);
+    static cudaError_t step_fast(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
+                                 const CUtensorMap &tmPo, const CUtensorMap &tmPc, int order, int flux,
+                                 int variant, cudaStream_t s);
 };
 
 cudaError_t launch_mass_final(const double *partial, int n, double *out, int *status, cudaStream_t s);

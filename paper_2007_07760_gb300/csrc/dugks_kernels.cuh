@@ -56,10 +56,19 @@ struct Store<float, __half> {
     static constexpr bool deviation = true;
 };
 
+// Storage layout of every plane: (ny + 2 GHOST) rows of `pitch` elements; cell
+// (x, y), 0 <= x < nx, 0 <= y < ny, sits at row y + GHOST, column x + GHOST.
+// The GHOST-wide border holds periodic copies, written by whichever kernel
+// writes the cell, so a tile plus its halo is always one rectangular box.
+constexpr int GHOST = 5;
+
 template <typename T>
 struct StepParams {
-    int nx, ny, pitch;          // pitch: elements between rows; planes are ny * pitch apart
+    int nx, ny, pitch;          // pitch: elements between rows
+    size_t plane;               // elements between planes = (ny + 2 GHOST) * pitch
+    int *status;                // sticky device flags (bit 0 non-finite, bit 1 wait timeout)
     int tiles_x;                // CTAs along x (mass partial index = by * tiles_x + bx)
+    int tile_w, tile_h;         // cells per CTA tile (mass partial kernel)
     const void *X;              // 9 planes in (storage type)
     const void *acc;            // KIND_T3B: accumulator planes (type T)
     const T *phi_cur;           // deviation storage: phi of X (authoritative)
@@ -82,6 +91,35 @@ struct StepParams {
     T t, t_old, t_face;         // time of X, of phi_old, of the faces
     T qscale, qinv;             // deviation storage scale s and 1 / s
 };
+
+template <typename T>
+__device__ __forceinline__ size_t gidx(const StepParams<T> &p, int x, int y) {
+    return (size_t)(y + GHOST) * p.pitch + (size_t)(x + GHOST);
+}
+
+// Writes v at cell (x, y) and at each of its periodic images inside the ghost border.
+template <typename T, typename V>
+__device__ __forceinline__ void put_cell(const StepParams<T> &p, V *plane, int x, int y, V v) {
+    plane[gidx(p, x, y)] = v;
+    const bool xl = x < GHOST, xh = x >= p.nx - GHOST, yl = y < GHOST, yh = y >= p.ny - GHOST;
+    if (!(xl | xh | yl | yh)) return;
+#pragma unroll
+    for (int ay = -1; ay <= 1; ay++) {
+        const int yy = y + ay * p.ny;
+        if (yy < -GHOST || yy >= p.ny + GHOST) continue;
+#pragma unroll
+        for (int ax = -1; ax <= 1; ax++) {
+            const int xx = x + ax * p.nx;
+            if ((ax == 0 && ay == 0) || xx < -GHOST || xx >= p.nx + GHOST) continue;
+            plane[gidx(p, xx, yy)] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ int wrapc(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
 
 // ---- prescribed velocity (Sec. II.A; Sec. III) ------------------------------
 template <typename T>
@@ -117,7 +155,7 @@ __device__ __forceinline__ void vel_analytic(const StepParams<T> &p, T x, T y, T
 template <typename T>
 __device__ __forceinline__ void vel_cell(const StepParams<T> &p, int gx, int gy, T t, T &u, T &v) {
     if (p.vel_kind == VEL_FIELD) {
-        const size_t c = (size_t)gy * p.pitch + gx;
+        const size_t c = gidx(p, gx, gy);
         u = p.ufield[c];
         v = p.vfield[c];
     } else {
@@ -132,7 +170,7 @@ __device__ __forceinline__ void vel_face(const StepParams<T> &p, int gx, int gy,
         int nxg = gx, nyg = gy;
         if (dir == 0) nxg = gx + 1 == p.nx ? 0 : gx + 1;
         else nyg = gy + 1 == p.ny ? 0 : gy + 1;
-        const size_t c0 = (size_t)gy * p.pitch + gx, c1 = (size_t)nyg * p.pitch + nxg;
+        const size_t c0 = gidx(p, gx, gy), c1 = gidx(p, nxg, nyg);
         u = T(0.5) * (p.ufield[c0] + p.ufield[c1]);
         v = T(0.5) * (p.vfield[c0] + p.vfield[c1]);
     } else if (dir == 0) {
@@ -275,8 +313,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
     T *sFb = sP + 2 * NC;                     // [9][2][NF]
     double *sred = reinterpret_cast<double *>(smem_raw + TL::red_offset);
 
-    const int nx = p.nx, ny = p.ny, pitch = p.pitch;
-    const size_t plane = (size_t)ny * pitch;
+    const int nx = p.nx, ny = p.ny;
+    const size_t plane = p.plane;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tid = threadIdx.x, nt = blockDim.x;
 
@@ -284,9 +322,9 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
     for (int idx = tid; idx < NH; idx += nt) {
         const int ly = idx / WH, lx = idx - ly * WH;
         int gx = x0 - H + lx, gy = y0 - H + ly;
-        gx = (gx % nx + nx) % nx;
-        gy = (gy % ny + ny) % ny;
-        const size_t g = (size_t)gy * pitch + gx;
+        gx = wrapc(gx, nx);
+        gy = wrapc(gy, ny);
+        const size_t g = gidx(p, gx, gy);
         if constexpr (DEV) {
             const __half *Xq = static_cast<const __half *>(p.X);
             const T ph = p.phi_cur[g];
@@ -313,8 +351,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
         const int rx = lx - (1 + R), ry = ly - (1 + R);       // relative to the tile origin
         const int hidx = (ry + H) * WH + (rx + H);
         int gx = x0 + rx, gy = y0 + ry;
-        gx = (gx % nx + nx) % nx;
-        gy = (gy % ny + ny) % ny;
+        gx = wrapc(gx, nx);
+        gy = wrapc(gy, ny);
         const T ph = sPhi[hidx];
         T gxp, gyp;
         grad_p<T, ORDER>(sPhi + hidx, WH, gxp, gyp);
@@ -332,7 +370,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
         if (p.useD) {  // d(phi u)/dt, backward difference
             T uo, vo;
             vel_cell(p, gx, gy, p.t_old, uo, vo);
-            const T po = p.phi_old[(size_t)gy * pitch + gx];
+            const T po = p.phi_old[gidx(p, gx, gy)];
             Dx = (ph * u - po * uo) * p.inv_dtD;
             Dy = (ph * v - po * vo) * p.inv_dtD;
         }
@@ -395,8 +433,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             phN += vN;
         }
         int gx = x0 + fx, gy = y0 + fy;
-        gx = (gx % nx + nx) % nx;
-        gy = (gy % ny + ny) % ny;
+        gx = wrapc(gx, nx);
+        gy = wrapc(gy, ny);
         T uE, vE_, uN, vN_;
         vel_face(p, gx, gy, 0, p.t_face, uE, vE_);
         vel_face(p, gx, gy, 1, p.t_face, uN, vN_);
@@ -422,7 +460,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
         const int ly = idx / TX, lx = idx - ly * TX;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= nx || gy >= ny) continue;
-        const size_t g = (size_t)gy * pitch + gx;
+        const size_t g = gidx(p, gx, gy);
         const int hidx = (ly + H) * WH + (lx + H);
         const int cidx = (ly + 1 + R) * WC + (lx + 1 + R);
         const int fidx = (ly + 1) * WF + (lx + 1);
@@ -462,27 +500,27 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
 #pragma unroll
             for (int k = 1; k < 9; k++) r += o2[k];
             o2[0] = (ph + p.ga2 * sumL) - r;
-            T *O2 = p.out2;
 #pragma unroll
-            for (int k = 0; k < 9; k++) O2[k * plane + g] = o2[k];
+            for (int k = 0; k < 9; k++) put_cell(p, p.out2 + k * plane, gx, gy, o2[k]);
         }
         if constexpr (DEV) {
             __half *Oq = static_cast<__half *>(p.out1);
 #pragma unroll
             for (int k = 0; k < 9; k++)
-                Oq[k * plane + g] = __float2half_rn((o1[k] - wq<T>(k) * phn) * (p.qscale * (T(1) / wq<T>(k))));
-            p.phi_out[g] = phn;
+                put_cell(p, Oq + k * plane, gx, gy,
+                         __float2half_rn((o1[k] - wq<T>(k) * phn) * (p.qscale * (T(1) / wq<T>(k)))));
+            put_cell(p, p.phi_out, gx, gy, phn);
             msum += (double)phn;
         } else {
             T *O = static_cast<T *>(p.out1);
-            double s = 0.0;
+            T s = T(0);
 #pragma unroll
             for (int k = 0; k < 9; k++) {
-                O[k * plane + g] = o1[k];
-                s += (double)o1[k];
+                put_cell(p, O + k * plane, gx, gy, o1[k]);
+                s += o1[k];
             }
-            if (KIND != KIND_T3B) p.phi_out[g] = ph;
-            msum += s;
+            if (KIND != KIND_T3B) put_cell(p, p.phi_out, gx, gy, ph);
+            msum += (double)s;
         }
     }
     if (p.mass_partial != nullptr) {
@@ -493,23 +531,22 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
 
 // ---- initial state: f = f^eq (Omega = 0), D = 0 ------------------------------
 // X = f^eq - frac * dt * S with frac = 1/2 (two-stage tilde f) or 1/4 (hat f).
+// phi0 uses the plane layout; only its cells (not its ghosts) are read.
 template <typename T, typename ST, int ORDER>
 __global__ void init_kernel(const StepParams<T> p, const T *phi0, T frac_dt) {
     constexpr bool DEV = Store<T, ST>::deviation;
     constexpr int R = ORDER == 4 ? 2 : 1;
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
     if (gx >= p.nx || gy >= p.ny) return;
-    const int nx = p.nx, ny = p.ny, pitch = p.pitch;
-    const size_t plane = (size_t)ny * pitch;
+    const int nx = p.nx, ny = p.ny;
+    const size_t plane = p.plane;
     // gather the (2R+1)^2 neighbourhood of phi0 into registers
     T nb[(2 * R + 1) * (2 * R + 1)];
 #pragma unroll
     for (int dy = -R; dy <= R; dy++)
 #pragma unroll
-        for (int dx = -R; dx <= R; dx++) {
-            const int xx = (gx + dx + nx) % nx, yy = (gy + dy + ny) % ny;
-            nb[(dy + R) * (2 * R + 1) + (dx + R)] = phi0[(size_t)yy * pitch + xx];
-        }
+        for (int dx = -R; dx <= R; dx++)
+            nb[(dy + R) * (2 * R + 1) + (dx + R)] = phi0[gidx(p, wrapc(gx + dx, nx), wrapc(gy + dy, ny))];
     const T *c = nb + R * (2 * R + 1) + R;
     T gxp, gyp;
     grad_p<T, ORDER>(c, 2 * R + 1, gxp, gyp);
@@ -525,7 +562,6 @@ __global__ void init_kernel(const StepParams<T> p, const T *phi0, T frac_dt) {
     T u, v;
     vel_cell(p, gx, gy, p.t, u, v);
     const T Vx = theta * nxv, Vy = theta * nyv;
-    const size_t g = (size_t)gy * pitch + gx;
     T fk[9];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
@@ -542,60 +578,53 @@ __global__ void init_kernel(const StepParams<T> p, const T *phi0, T frac_dt) {
         __half *Oq = static_cast<__half *>(p.out1);
 #pragma unroll
         for (int k = 0; k < 9; k++)
-            Oq[k * plane + g] = __float2half_rn((fk[k] - wq<T>(k) * phn) * (p.qscale * (T(1) / wq<T>(k))));
-        p.phi_out[g] = phn;
+            put_cell(p, Oq + k * plane, gx, gy,
+                     __float2half_rn((fk[k] - wq<T>(k) * phn) * (p.qscale * (T(1) / wq<T>(k)))));
+        put_cell(p, p.phi_out, gx, gy, phn);
     } else {
         T *O = static_cast<T *>(p.out1);
 #pragma unroll
-        for (int k = 0; k < 9; k++) O[k * plane + g] = fk[k];
+        for (int k = 0; k < 9; k++) put_cell(p, O + k * plane, gx, gy, fk[k]);
+        put_cell(p, p.phi_out, gx, gy, ph);   // phi of the previous level for d(phi u)/dt
     }
 }
 
-// ---- mass: per-tile FP64 partials in the step kernels' tiling, then one CTA --
-template <typename T, typename ST, int TX, int TY>
+// sum_k X_k of one cell (the cell's phi), in the storage's arithmetic type
+template <typename T, typename ST>
+__device__ __forceinline__ T cell_phi(const StepParams<T> &p, size_t g) {
+    if constexpr (Store<T, ST>::deviation) {
+        return p.phi_cur[g];
+    } else {
+        const T *Xf = static_cast<const T *>(p.X);
+        T s = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; k++) s += Xf[k * p.plane + g];
+        return s;
+    }
+}
+
+// ---- mass: per-tile FP64 partials in the step kernel's tiling, then one CTA --
+template <typename T, typename ST>
 __global__ void __launch_bounds__(256) mass_partial_kernel(const StepParams<T> p) {
     __shared__ double sred[32];
-    constexpr bool DEV = Store<T, ST>::deviation;
-    const size_t plane = (size_t)p.ny * p.pitch;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * p.tile_w, y0 = blockIdx.y * p.tile_h;
     double msum = 0.0;
-    for (int idx = threadIdx.x; idx < TX * TY; idx += blockDim.x) {
-        const int ly = idx / TX, lx = idx - ly * TX;
+    for (int idx = threadIdx.x; idx < p.tile_w * p.tile_h; idx += blockDim.x) {
+        const int ly = idx / p.tile_w, lx = idx - ly * p.tile_w;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= p.nx || gy >= p.ny) continue;
-        const size_t g = (size_t)gy * p.pitch + gx;
-        if constexpr (DEV) {
-            msum += (double)p.phi_cur[g];
-        } else {
-            const T *Xf = static_cast<const T *>(p.X);
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < 9; k++) s += (double)Xf[k * plane + g];
-            msum += s;
-        }
+        msum += (double)cell_phi<T, ST>(p, gidx(p, gx, gy));
     }
     const double s = block_sum(msum, sred);
     if (threadIdx.x == 0) p.mass_partial[blockIdx.y * p.tiles_x + blockIdx.x] = s;
 }
 
-// phi of the state into a T plane (pitch-free, ny * nx)
+// phi of the state into a dense ny * nx array of T
 template <typename T, typename ST>
 __global__ void phi_kernel(const StepParams<T> p, T *out) {
-    constexpr bool DEV = Store<T, ST>::deviation;
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
     if (gx >= p.nx || gy >= p.ny) return;
-    const size_t g = (size_t)gy * p.pitch + gx;
-    const size_t plane = (size_t)p.ny * p.pitch;
-    T ph;
-    if constexpr (DEV) {
-        ph = p.phi_cur[g];
-    } else {
-        const T *Xf = static_cast<const T *>(p.X);
-        ph = T(0);
-#pragma unroll
-        for (int k = 0; k < 9; k++) ph += Xf[k * plane + g];
-    }
-    out[(size_t)gy * p.nx + gx] = ph;
+    out[(size_t)gy * p.nx + gx] = cell_phi<T, ST>(p, gidx(p, gx, gy));
 }
 
 }  // namespace dugks

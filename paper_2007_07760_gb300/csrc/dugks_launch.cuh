@@ -66,9 +66,62 @@ cudaError_t Launch<T, ST>::init(const StepParams<T> &p, const T *phi0, T frac_dt
 
 template <typename T, typename ST>
 cudaError_t Launch<T, ST>::mass_partial(const StepParams<T> &p, cudaStream_t s) {
-    dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TILE_Y - 1) / TILE_Y);
-    mass_partial_kernel<T, ST, TILE_X, TILE_Y><<<grid, STEP_THREADS, 0, s>>>(p);
+    dim3 grid((p.nx + p.tile_w - 1) / p.tile_w, (p.ny + p.tile_h - 1) / p.tile_h);
+    mass_partial_kernel<T, ST><<<grid, 256, 0, s>>>(p);
     return cudaGetLastError();
+}
+
+// rows of cells per thread in the fast kernel: 4 (FP32 arithmetic) or 2 (FP64)
+template <typename T>
+constexpr int fast_mr() { return sizeof(T) == 8 ? 2 : 4; }
+
+template <typename T, typename ST, int NW, int MR>
+static FastGeom geom_t() {
+    using FT = FastTile<T, ST, NW, MR>;
+    return FastGeom{FT::NT, FT::TX, FT::TY, FT::BW, FT::RH, FT::BWT};
+}
+
+// variant 0: 8 warps, several rows per thread (large grids); variant 1: 16 warps,
+// one row per thread (small grids: more warps per SM to hide latency)
+template <typename T, typename ST>
+FastGeom Launch<T, ST>::fast_geom(int variant) {
+    return variant == 0 ? geom_t<T, ST, 8, fast_mr<T>()>() : geom_t<T, ST, 16, 1>();
+}
+
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
+static cudaError_t launch_fast_t(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
+                                 const CUtensorMap &tmPo, const CUtensorMap &tmPc, cudaStream_t s) {
+    using FT = FastTile<T, ST, NW, MR>;
+    auto kern = step_fast_kernel<T, ST, ORDER, FLUX, NW, MR>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FT::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((p.nx + FT::TX - 1) / FT::TX, (p.ny + FT::TY - 1) / FT::TY);
+    kern<<<grid, FT::NT, FT::smem_bytes, s>>>(p, cf, fe, tmX, tmPo, tmPc);
+    return cudaGetLastError();
+}
+
+template <typename T, typename ST, int ORDER, int FLUX>
+static cudaError_t launch_fast_v(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
+                                 const CUtensorMap &tmPo, const CUtensorMap &tmPc, int variant, cudaStream_t s) {
+    return variant == 0 ? launch_fast_t<T, ST, ORDER, FLUX, 8, fast_mr<T>()>(p, cf, fe, tmX, tmPo, tmPc, s)
+                        : launch_fast_t<T, ST, ORDER, FLUX, 16, 1>(p, cf, fe, tmX, tmPo, tmPc, s);
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::step_fast(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
+                                     const CUtensorMap &tmPo, const CUtensorMap &tmPc, int order, int flux,
+                                     int variant, cudaStream_t s) {
+    if (order == 2)
+        return flux == 0 ? launch_fast_v<T, ST, 2, 0>(p, cf, fe, tmX, tmPo, tmPc, variant, s)
+                         : launch_fast_v<T, ST, 2, 1>(p, cf, fe, tmX, tmPo, tmPc, variant, s);
+    if (order == 3)
+        return flux == 0 ? launch_fast_v<T, ST, 3, 0>(p, cf, fe, tmX, tmPo, tmPc, variant, s)
+                         : launch_fast_v<T, ST, 3, 1>(p, cf, fe, tmX, tmPo, tmPc, variant, s);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T, typename ST>
