@@ -7,6 +7,7 @@
 #include <cudaTypedefs.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -545,8 +546,15 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
         const FastGeom big = p->precision == DUGKS_FP64 ? Launch<double, double>::fast_geom(0)
                              : p->precision == DUGKS_FP32 ? Launch<float, float>::fast_geom(0)
                                                           : Launch<float, __half>::fast_geom(0);
-        const long tiles = (long)((p->nx + big.tile_w - 1) / big.tile_w) * ((p->ny + big.tile_h - 1) / big.tile_h);
-        c->variant = tiles >= 2L * sms ? 0 : 1;   // small grids: smaller tiles to fill the SMs
+        (void)big;
+        (void)sms;
+        // 8 warps x 2 rows per thread measured fastest from 256^2 to 2048^2 (FP32)
+        c->variant = 2;
+        // tuning override (set by the autotuner): DUGKS_FAST_VARIANT = 0..3
+        if (const char *ev = std::getenv("DUGKS_FAST_VARIANT")) {
+            const int v = std::atoi(ev);
+            if (v >= 0 && v < FAST_VARIANTS) c->variant = v;
+        }
     }
     bool ok = true;
     for (int s = 0; s < c->nsets && ok; s++) {

@@ -37,6 +37,19 @@ struct FaceCoefs {
     T n[9][4][4];
 };
 
+// structural non-zeros of the face stencils (the host fills the same pattern);
+// b, a are row and column offsets from the face-owner cell
+__host__ __device__ constexpr bool tapE(int flux, int k, int b, int a) {
+    // b in -1..1, a in -1..2
+    return flux == 0 ? (ex(k) > 0 ? a <= 1 : ex(k) < 0 ? a >= 0 : true)
+                     : (ey(k) == 0 ? (b == 0 && (a == 0 || a == 1)) : (b != 0 || a == 0 || a == 1));
+}
+__host__ __device__ constexpr bool tapN(int flux, int k, int b, int a) {
+    // b in -1..2, a in -1..1
+    return flux == 0 ? (ey(k) > 0 ? b <= 1 : ey(k) < 0 ? b >= 0 : true)
+                     : (ex(k) == 0 ? (a == 0 && (b == 0 || b == 1)) : (a != 0 || b == 0 || b == 1));
+}
+
 // Per-step scalars of the fast kernel that the generic parameters do not carry.
 template <typename T>
 struct FastExtra {
@@ -106,6 +119,44 @@ __device__ __noinline__ void put_ghosts(const StepParams<T> &p, V *plane, int x,
             const int xx = x + ax * p.nx;
             if ((ax == 0 && ay == 0) || xx < -GHOST || xx >= p.nx + GHOST) continue;
             plane[gidx(p, xx, yy)] = v;
+        }
+    }
+}
+
+// four consecutive shared-memory values (16-B aligned for float, two 16-B loads for double)
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+    const double2 q0 = reinterpret_cast<const double2 *>(p)[0], q1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// ghost images of the 9 distribution values and phi of one cell near an edge
+// (values by argument so that the caller's registers stay registers)
+template <typename T, typename V>
+__device__ __noinline__ void put_ghosts9(const StepParams<T> &p, V *out, int x, int y, T phi, V v0, V v1, V v2,
+                                         V v3, V v4, V v5, V v6, V v7, V v8) {
+#pragma unroll 1
+    for (int ay = -1; ay <= 1; ay++) {
+        const int yy = y + ay * p.ny;
+        if (yy < -GHOST || yy >= p.ny + GHOST) continue;
+#pragma unroll 1
+        for (int ax = -1; ax <= 1; ax++) {
+            const int xx = x + ax * p.nx;
+            if ((ax == 0 && ay == 0) || xx < -GHOST || xx >= p.nx + GHOST) continue;
+            const size_t g = gidx(p, xx, yy), pl = p.plane;
+            out[g] = v0;
+            out[pl + g] = v1;
+            out[2 * pl + g] = v2;
+            out[3 * pl + g] = v3;
+            out[4 * pl + g] = v4;
+            out[5 * pl + g] = v5;
+            out[6 * pl + g] = v6;
+            out[7 * pl + g] = v7;
+            out[8 * pl + g] = v8;
+            p.phi_out[g] = phi;
         }
     }
 }
@@ -234,15 +285,6 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
 
     // accessors (relative cell coordinates x, y of the tile)
     auto xidx = [&](int x, int y) { return (y + 3) * BW + (x + 3 + ox); };   // + k * RH * BW
-    auto Xat = [&](int k, int x, int y) -> T {
-        const ST v = sX[k * RH * BW + xidx(x, y)];
-        if constexpr (DEV) {
-            const T ph = sPc[(y + 3) * BWT + (x + 3 + oxt)];
-            return sK[k * 4 + 2] * (ph + to_f(v) * p.qinv);
-        } else {
-            return (T)v;
-        }
-    };
     auto PHI = [&](int x, int y) -> T {
         if constexpr (DEV) return sPc[(y + 3) * BWT + (x + 3 + oxt)];
         else return sPhi[(y + 3) * RW + (x + 3)];
@@ -299,13 +341,14 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
 
     // ---- S1: phi = sum_k X_k on the state region (Eq. (30)) ------------------
     if constexpr (!DEV) {
-        for (int idx = tid; idx < RW * RH; idx += NT) {
-            const int y = idx / RW - 3, x = idx - (y + 3) * RW - 3;
-            T s = T(0);
+        for (int y = warp - 3; y < RH - 3; y += NW)
+            for (int x = lane - 3; x < RW - 3; x += 32) {
+                const int xi = xidx(x, y);
+                T s = T(0);
 #pragma unroll
-            for (int k = 0; k < 9; k++) s += (T)sX[k * RH * BW + xidx(x, y)];
-            sPhi[idx] = s;
-        }
+                for (int k = 0; k < 9; k++) s += (T)sX[k * RH * BW + xi];
+                sPhi[(y + 3) * RW + (x + 3)] = s;
+            }
     }
     __syncthreads();
 
@@ -315,30 +358,26 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
     T cg[MR], cPx[MR], cPy[MR];
 #pragma unroll
     for (int r = 0; r < MR; r++) cell_q(fx, fy0 + r, cg[r], cPx[r], cPy[r]);
-    int exj[NXS], exx[NXS], exy[NXS];
+    // extra cells are clamped to the last one: surplus threads recompute it and
+    // store identical values (no divergent branch in the direction loop)
+    int exj[NXS], exX[NXS];
     T eg[NXS], ePx[NXS], ePy[NXS];
 #pragma unroll
     for (int s = 0; s < NXS; s++) {
-        const int e = tid + s * NT;
-        exj[s] = -1;
-        exx[s] = exy[s] = 0;
-        eg[s] = ePx[s] = ePy[s] = T(0);
-        if (e < NE) {
-            int x, y;
-            if (e < 3 * CH) {
-                const int c = e / CH;
-                x = c == 0 ? -2 : TX + c - 1;
-                y = e - c * CH - 2;
-            } else {
-                const int e2 = e - 3 * CH, c = e2 >> 5;
-                y = c == 0 ? -2 : TY + c - 1;
-                x = (e2 & 31) - 1;
-            }
-            exx[s] = x;
-            exy[s] = y;
-            exj[s] = (y + 2) * CW + (x + 2);
-            cell_q(x, y, eg[s], ePx[s], ePy[s]);
+        const int e = min(tid + s * NT, NE - 1);
+        int x, y;
+        if (e < 3 * CH) {
+            const int c = e / CH;
+            x = c == 0 ? -2 : TX + c - 1;
+            y = e - c * CH - 2;
+        } else {
+            const int e2 = e - 3 * CH, c = e2 >> 5;
+            y = c == 0 ? -2 : TY + c - 1;
+            x = (e2 & 31) - 1;
         }
+        exj[s] = (y + 2) * CW + (x + 2);
+        exX[s] = xidx(x, y);
+        cell_q(x, y, eg[s], ePx[s], ePy[s]);
     }
 
     // ---- S3: directions ------------------------------------------------------
@@ -346,7 +385,7 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
 #pragma unroll
     for (int r = 0; r < MR; r++) phbE[r] = phbN[r] = sumD[r] = T(0);
     const T gmc = p.ga1 * (T(1) - p.c2);    // gamma (1 - c2)
-    T fn0Prev = T(0), eyPrev = T(0);        // pending south difference of my first row
+    T fn0Prev = T(0);                       // pending south difference of my first row
     const int fbase = (fy0 + 2) * CW + (fx + 2);     // my first cell in the cell-quantity region
     const int xbase = xidx(fx, fy0);                 // ... in the state box
 
@@ -356,49 +395,58 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
         else return reinterpret_cast<T *>(sX)[k * RH * BW + xbase + r * BW];
     };
 
-#pragma unroll 1
+    // The direction loop is unrolled: xi_k, w_k, the stencil coefficients (kernel
+    // parameters, i.e. constant-bank operands) and the structural zeros of each
+    // face stencil are compile-time per direction.
+#pragma unroll
     for (int k = 0; k < 9; k++) {
         T *F = sF + (k & 1) * NC;
-        const T exk = sK[k * 4 + 0], eyk = sK[k * 4 + 1], wk = sK[k * 4 + 2];
+        constexpr T one = T(1);
+        const int kx = ex(k), ky = ey(k);
+        const T wk = wq<T>(k);
+        // xi_k . P without multiplications by 0 or +-1
+        auto xiP = [&](T px, T py) -> T {
+            T v = T(0);
+            if (kx > 0) v = px;
+            if (kx < 0) v = -px;
+            if (ky > 0) v = (kx != 0) ? v + py : py;
+            if (ky < 0) v = (kx != 0) ? v - py : -py;
+            return v;
+        };
         // S3a: bar f^+_k = X_k + b (g_k - X_k) (increment form; a + b = 1)
         T xk[MR], gk[MR];
 #pragma unroll
         for (int r = 0; r < MR; r++) {
-            xk[r] = Xat(k, fx, fy0 + r);
-            gk[r] = wk * (cg[r] + (exk * cPx[r] + eyk * cPy[r]));
+            const ST v = sX[k * RH * BW + xbase + r * BW];
+            if constexpr (DEV) xk[r] = wk * (cg[r] + to_f(v) * p.qinv);
+            else xk[r] = (T)v;
+            gk[r] = wk * (cg[r] + xiP(cPx[r], cPy[r]));
             F[fbase + r * CW] = xk[r] + p.b * (gk[r] - xk[r]);
         }
 #pragma unroll
         for (int s = 0; s < NXS; s++) {
-            if (exj[s] >= 0) {
-                const T xe = Xat(k, exx[s], exy[s]);
-                const T ge = wk * (eg[s] + (exk * ePx[s] + eyk * ePy[s]));
-                F[exj[s]] = xe + p.b * (ge - xe);
-            }
+            const ST v = sX[k * RH * BW + exX[s]];
+            T xe;
+            if constexpr (DEV) xe = wk * (eg[s] + to_f(v) * p.qinv);
+            else xe = (T)v;
+            const T ge = wk * (eg[s] + xiP(ePx[s], ePy[s]));
+            F[exj[s]] = xe + p.b * (ge - xe);
         }
         __syncthreads();
         // finish the previous direction's first-row partial with its south difference
-        if (k > 1 && fx >= 0 && fy0 >= 0) {
-            const T below = sNB[((k - 1) & 1) * NW * 32 + (warp - 1) * 32 + lane];
-            const T d = eyPrev * (fn0Prev - below);
+        if (k > 1 && ey(k - 1) != 0) {   // (warp 0 reads a neighbour slot; its row -1 result is never stored)
+            const T below = sNB[((k - 1) & 1) * NW * 32 + (warp > 0 ? warp - 1 : 0) * 32 + lane];
+            const T d = ey(k - 1) > 0 ? (fn0Prev - below) : (below - fn0Prev);
             part_ref(k - 1, 0) -= gmc * d;
             sumD[0] += d;
         }
         // S3b: face values of my MR cells from a (MR + 3) x 4 window of bar f^+_k
+        // (entries no tap uses are never loaded)
         T win[MR + 3][4];
 #pragma unroll
         for (int i = 0; i < MR + 3; i++)
 #pragma unroll
             for (int a = 0; a < 4; a++) win[i][a] = F[fbase + (i - 1) * CW + (a - 1)];
-        T cE[3][4], cN[4][3];
-#pragma unroll
-        for (int b = 0; b < 3; b++)
-#pragma unroll
-            for (int a = 0; a < 4; a++) cE[b][a] = sCE[(k * 3 + b) * 4 + a];
-#pragma unroll
-        for (int b = 0; b < 4; b++)
-#pragma unroll
-            for (int a = 0; a < 3; a++) cN[b][a] = sCN[(k * 4 + b) * 4 + a];
         T fe[MR], fn[MR];
 #pragma unroll
         for (int r = 0; r < MR; r++) {
@@ -406,11 +454,13 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
 #pragma unroll
             for (int b = 0; b < 3; b++)
 #pragma unroll
-                for (int a = 0; a < 4; a++) se += cE[b][a] * win[r + b][a];
+                for (int a = 0; a < 4; a++)
+                    if (tapE(FLUX, k, b - 1, a - 1)) se += cf.e[k][b][a] * win[r + b][a];
 #pragma unroll
             for (int b = 0; b < 4; b++)
 #pragma unroll
-                for (int a = 0; a < 3; a++) sn += cN[b][a] * win[r + b][a];
+                for (int a = 0; a < 3; a++)
+                    if (tapN(FLUX, k, b - 1, a - 1)) sn += cf.n[k][b][a] * win[r + b][a];
             fe[r] = se;
             fn[r] = sn;
             phbE[r] += se;
@@ -418,24 +468,28 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
         }
         // Dbar_k = xi_x (f_E(c) - f_E(c - E)) + xi_y (f_N(c) - f_N(c - N)); partial update
         // (direction 0 has xi = 0 and is completed from phi in S4)
+        if (k > 0) {
 #pragma unroll
-        for (int r = 0; r < MR; r++) {
-            const T left = __shfl_up_sync(0xffffffffu, fe[r], 1);
-            T d = exk * (fe[r] - left);
-            if (r > 0) d += eyk * (fn[r] - fn[r - 1]);
-            if (k > 0 && fx >= 0 && fy0 + r >= 0) {
+            for (int r = 0; r < MR; r++) {
+                T d = T(0);
+                if (kx != 0) {
+                    const T left = __shfl_up_sync(0xffffffffu, fe[r], 1);
+                    d = kx > 0 ? fe[r] - left : left - fe[r];
+                }
+                if (ky != 0 && r > 0) d = ky > 0 ? d + (fn[r] - fn[r - 1]) : d - (fn[r] - fn[r - 1]);
+                // cells outside the tile write harmless values
                 part_ref(k, r) = xk[r] + p.be1 * (gk[r] - xk[r]) - gmc * d;
                 sumD[r] += d;
             }
         }
+        (void)one;
         fn0Prev = fn[0];
-        eyPrev = eyk;
-        sNB[(k & 1) * NW * 32 + warp * 32 + lane] = fn[MR - 1];
+        if (ky != 0) sNB[(k & 1) * NW * 32 + warp * 32 + lane] = fn[MR - 1];
     }
     __syncthreads();
-    if (fx >= 0 && fy0 >= 0) {
-        const T below = sNB[(8 & 1) * NW * 32 + (warp - 1) * 32 + lane];
-        const T d = eyPrev * (fn0Prev - below);
+    if (ey(8) != 0) {
+        const T below = sNB[(8 & 1) * NW * 32 + (warp > 0 ? warp - 1 : 0) * 32 + lane];
+        const T d = ey(8) > 0 ? (fn0Prev - below) : (below - fn0Prev);
         part_ref(8, 0) -= gmc * d;
         sumD[0] += d;
     }
@@ -504,23 +558,21 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
         o[0] = phn - rsum;
         if constexpr (DEV) {
             __half *Oq = static_cast<__half *>(p.out1);
+            __half qv[9];
 #pragma unroll
             for (int k = 0; k < 9; k++) {
-                const __half qv = __float2half_rn((o[k] - wq<T>(k) * phn) * (p.qscale / wq<T>(k)));
-                Oq[k * plane + g] = qv;
-                if (edge) put_ghosts(p, Oq + k * plane, gx, gy, qv);
+                qv[k] = __float2half_rn((o[k] - wq<T>(k) * phn) * (p.qscale / wq<T>(k)));
+                Oq[k * plane + g] = qv[k];
             }
             p.phi_out[g] = phn;
-            if (edge) put_ghosts(p, p.phi_out, gx, gy, phn);
+            if (edge)
+                put_ghosts9(p, Oq, gx, gy, phn, qv[0], qv[1], qv[2], qv[3], qv[4], qv[5], qv[6], qv[7], qv[8]);
         } else {
             T *O = static_cast<T *>(p.out1);
 #pragma unroll
-            for (int k = 0; k < 9; k++) {
-                O[k * plane + g] = o[k];
-                if (edge) put_ghosts(p, O + k * plane, gx, gy, o[k]);
-            }
+            for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
             p.phi_out[g] = cg[r];
-            if (edge) put_ghosts(p, p.phi_out, gx, gy, cg[r]);
+            if (edge) put_ghosts9(p, O, gx, gy, cg[r], o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
         }
         msum += (double)phn;
     }

@@ -16,7 +16,12 @@ constexpr int TILE_X = 32;
 constexpr int TILE_Y = 8;
 constexpr int STEP_THREADS = 256;
 
-// Geometry of a TMA-staged (fast) variant: 0 = 8 warps per CTA, 1 = 4 warps.
+// Fast-kernel variants (warps per CTA x rows per thread): 0 = 8 x 4 (FP64: 8 x 2),
+// 1 = 16 x 1, 2 = 8 x 2, 3 = 16 x 2. Fewer rows per thread: fewer registers and
+// more resident warps, more halo overhead.
+constexpr int FAST_VARIANTS = 4;
+
+// Geometry of a TMA-staged (fast) variant.
 struct FastGeom {
     int threads, tile_w, tile_h;   // cells written per CTA
     int box_w, box_h;              // state box (elements, rows)

@@ -81,11 +81,14 @@ static FastGeom geom_t() {
     return FastGeom{FT::NT, FT::TX, FT::TY, FT::BW, FT::RH, FT::BWT};
 }
 
-// variant 0: 8 warps, several rows per thread (large grids); variant 1: 16 warps,
-// one row per thread (small grids: more warps per SM to hide latency)
 template <typename T, typename ST>
 FastGeom Launch<T, ST>::fast_geom(int variant) {
-    return variant == 0 ? geom_t<T, ST, 8, fast_mr<T>()>() : geom_t<T, ST, 16, 1>();
+    switch (variant) {
+    case 1: return geom_t<T, ST, 16, 1>();
+    case 2: return geom_t<T, ST, 8, 2>();
+    case 3: return geom_t<T, ST, 16, 2>();
+    default: return geom_t<T, ST, 8, fast_mr<T>()>();
+    }
 }
 
 template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
@@ -105,10 +108,15 @@ static cudaError_t launch_fast_t(const StepParams<T> &p, const FaceCoefs<T> &cf,
 }
 
 template <typename T, typename ST, int ORDER, int FLUX>
-static cudaError_t launch_fast_v(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
-                                 const CUtensorMap &tmPo, const CUtensorMap &tmPc, int variant, cudaStream_t s) {
-    return variant == 0 ? launch_fast_t<T, ST, ORDER, FLUX, 8, fast_mr<T>()>(p, cf, fe, tmX, tmPo, tmPc, s)
-                        : launch_fast_t<T, ST, ORDER, FLUX, 16, 1>(p, cf, fe, tmX, tmPo, tmPc, s);
+static cudaError_t launch_fast_v(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,
+                                 const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc, int variant,
+                                 cudaStream_t s) {
+    switch (variant) {
+    case 1: return launch_fast_t<T, ST, ORDER, FLUX, 16, 1>(p, cf, fe, tmX, tmPo, tmPc, s);
+    case 2: return launch_fast_t<T, ST, ORDER, FLUX, 8, 2>(p, cf, fe, tmX, tmPo, tmPc, s);
+    case 3: return launch_fast_t<T, ST, ORDER, FLUX, 16, 2>(p, cf, fe, tmX, tmPo, tmPc, s);
+    default: return launch_fast_t<T, ST, ORDER, FLUX, 8, fast_mr<T>()>(p, cf, fe, tmX, tmPo, tmPc, s);
+    }
 }
 
 template <typename T, typename ST>
