@@ -137,6 +137,60 @@ int dugks_load_state(dugks_ctx *c, const void *host, size_t bytes, int64_t step_
 /* Frees everything; NULL-safe; waits for the context's outstanding work. */
 void dugks_destroy(dugks_ctx *c);
 
+/* ---- many grids per launch ------------------------------------------------
+ * A batch advances many independent periodic grids of different sizes with one
+ * launch per step: a work list of 31-cell-wide tiles of all grids is processed
+ * by a grid-stride set of CTAs (the TMA-staged two-stage kernel), followed by a
+ * per-grid FP64 mass and step-counter update. Each grid keeps its own step
+ * counter on the device, so grids may join (dugks_batch_add) and leave
+ * (dugks_batch_remove) between calls of dugks_batch_step, and a sequence of
+ * steps is replayed as a CUDA graph. Every grid's result is bitwise the same
+ * whatever else is in the batch. Two-stage scheme, orders 2 and 3 only. */
+typedef struct dugks_batch dugks_batch;
+
+/* Common parameters of all grids (nx, ny ignored; stages must be 2, order 2 or
+ * 3). cuda_stream as in dugks_create. */
+int dugks_batch_create(const dugks_params *common, void *cuda_stream, dugks_batch **out);
+
+/* Device bytes one grid of nx * ny cells needs in a batch (admission control). */
+size_t dugks_batch_grid_bytes(const dugks_params *common, int32_t nx, int32_t ny);
+
+/* Adds a grid: phi0_host (ny * nx doubles), velocity kind UNIFORM, ROTATION or
+ * VORTEX with its parameters (as dugks_set_velocity), and the number of steps
+ * after which the grid stops advancing (target_steps < 0: unbounded). Builds
+ * the initial equilibrium. *grid_id receives a non-negative id. DUGKS_ENOMEM
+ * if the device memory is not available. */
+int dugks_batch_add(dugks_batch *b, int32_t nx, int32_t ny, const double *phi0_host, int vel_kind,
+                    const double *vel_params, int64_t target_steps, int32_t *grid_id);
+
+/* Removes a grid and frees its device memory (waits for the stream). */
+int dugks_batch_remove(dugks_batch *b, int32_t grid_id);
+
+/* Enqueues nsteps steps of every grid that has not reached its target. */
+int dugks_batch_step(dugks_batch *b, int64_t nsteps);
+
+/* Steps taken by a grid (host mirror of its device counter). */
+int64_t dugks_batch_step_index(const dugks_batch *b, int32_t grid_id);
+
+/* Waits and copies phi (ny * nx doubles) of one grid to the host. */
+int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host);
+
+/* Waits and returns one grid's mass (FP64, fixed-order sum). */
+int dugks_batch_mass(dugks_batch *b, int32_t grid_id, double *out);
+
+/* Tile variant of the kernel (0..3; see the design notes); rebuilds descriptors. */
+int dugks_batch_set_variant(dugks_batch *b, int variant);
+
+/* Cells of all grids that are still advancing. */
+int64_t dugks_batch_active_cells(const dugks_batch *b);
+
+/* Waits and returns the sticky status; text of the last error. */
+int dugks_batch_status(dugks_batch *b);
+const char *dugks_batch_last_error(const dugks_batch *b);
+
+/* Frees everything (NULL-safe). */
+void dugks_batch_destroy(dugks_batch *b);
+
 /* Allocation-free FP64 sum of a device field. The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc where they need a mass,
  * such as code running while a stream is captured into a CUDA graph, hosts

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdugks.so")
-SOURCES = ["dugks_api.cu", "dugks_inst_f64.cu", "dugks_inst_f32.cu", "dugks_inst_f16.cu", "dugks_noalloc.cu"]
+SOURCES = ["dugks_api.cu", "dugks_inst_f64.cu", "dugks_inst_f32.cu", "dugks_inst_f16.cu", "dugks_noalloc.cu", "dugks_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

@@ -1,0 +1,626 @@
+// dugks_batch.cu -- many independent grids per launch (declared in include/dugks.h).
+//
+// Host side of the batch: per-grid device memory and descriptors (BatchGrid,
+// with TMA tensor maps), the work list of tiles, the per-step launches and
+// their CUDA-graph replay. The arithmetic is the fast kernel's, unchanged.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dugks.h"
+#include "dugks_host.h"
+#include "dugks_internal.h"
+
+using namespace dugks;
+using namespace dugks::host;
+
+namespace {
+
+struct Slot {
+    bool used = false;
+    int nx = 0, ny = 0, pitch = 0, tiles_x = 0, tiles_y = 0;
+    size_t plane = 0;
+    void *X[2] = {nullptr, nullptr};
+    void *phi[3] = {nullptr, nullptr, nullptr};
+    int64_t step = 0, target = -1;
+    int vel_kind = DUGKS_VEL_UNIFORM;
+    double vel[3] = {0, 0, 0};
+    bool mass_known = false;
+};
+
+constexpr int GRAPH_STEPS = 8;
+
+}  // namespace
+
+struct dugks_batch {
+    dugks_params p{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t tsize = 4, ssize = 4;
+    int nphi = 2;
+    int variant = 2;
+    int ctas = 0;
+    std::vector<Slot> slots;
+    // device side
+    void *d_grids = nullptr;
+    int grids_cap = 0;
+    int4 *d_items = nullptr;
+    int items_cap = 0, nitems = 0;
+    double *d_partials = nullptr;
+    double *d_mass = nullptr;
+    int *d_status = nullptr;
+    void *d_tmp = nullptr;       // phi read-out / generic mass partials
+    size_t tmp_bytes = 0;
+    std::vector<unsigned char> h_grids;   // staging of the descriptors
+    std::vector<int4> h_items;
+    bool dirty = true;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<unsigned char> coefs, uniform;
+    int sticky = DUGKS_OK;
+    std::string err;
+};
+
+namespace {
+
+int bfail(dugks_batch *b, int code, const std::string &msg) {
+    if (b) {
+        if (b->sticky == DUGKS_OK) b->sticky = code;
+        b->err = msg;
+    }
+    return code;
+}
+int bcuda(dugks_batch *b, cudaError_t e, const char *where) {
+    return bfail(b, DUGKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool fp64(const dugks_batch *b) { return b->p.precision == DUGKS_FP64; }
+
+size_t plane_of(int nx, int ny, int *pitch_out) {
+    const int pitch = (nx + 2 * GHOST + 31) / 32 * 32;
+    if (pitch_out) *pitch_out = pitch;
+    return (size_t)(ny + 2 * GHOST) * pitch;
+}
+
+template <typename T, typename ST>
+FastGeom geom(const dugks_batch *b) { return Launch<T, ST>::fast_geom(b->variant); }
+
+FastGeom batch_geom(const dugks_batch *b) {
+    switch (b->p.precision) {
+    case DUGKS_FP64: return geom<double, double>(b);
+    case DUGKS_FP32: return geom<float, float>(b);
+    default: return geom<float, __half>(b);
+    }
+}
+
+int resident_ctas(dugks_batch *b) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
+    int per = 1;
+    switch (b->p.precision) {
+    case DUGKS_FP64: per = Launch<double, double>::batch_ctas_per_sm(b->p.order, b->p.flux, b->variant); break;
+    case DUGKS_FP32: per = Launch<float, float>::batch_ctas_per_sm(b->p.order, b->p.flux, b->variant); break;
+    default: per = Launch<float, __half>::batch_ctas_per_sm(b->p.order, b->p.flux, b->variant); break;
+    }
+    return std::max(1, sms) * std::max(1, per);
+}
+
+template <typename T>
+void fill_uniform(dugks_batch *b, const FastGeom &g) {
+    BatchUniform<T> u;
+    std::memset(&u, 0, sizeof u);
+    const double dt = b->p.cfl, tau = 3.0 * b->p.M, h = 0.5 * dt;
+    const double bb = (dt + h) / (2.0 * tau + dt);   // bar f^+ = X + b (g - X)
+    u.b = (T)bb;
+    u.h = (T)h;
+    u.c1 = (T)(2.0 * tau / (2.0 * tau + h));
+    u.c2 = (T)(h / (2.0 * tau + h));
+    u.c3 = (T)(tau * h / (2.0 * tau + h));
+    u.be1 = (T)(4.0 / 3.0 * bb);
+    u.ga1 = (T)dt;
+    u.tau = (T)tau;
+    u.theta_c = (T)(-4.0 / (b->p.W * (b->p.phiA - b->p.phiB)));
+    u.phiA = (T)b->p.phiA;
+    u.phiB = (T)b->p.phiB;
+    u.inv_dt = (T)(1.0 / dt);
+    u.qscale = (T)256.0;
+    u.qinv = (T)(1.0 / 256.0);
+    u.dt = dt;
+    u.dtphiu = b->p.dtphiu;
+    u.tile_w = g.tile_w;
+    u.tile_h = g.tile_h;
+    u.status = b->d_status;
+    b->uniform.assign(reinterpret_cast<unsigned char *>(&u), reinterpret_cast<unsigned char *>(&u) + sizeof u);
+    FaceCoefs<T> cf = make_face_coefs<T>(b->p.order, b->p.flux, h);
+    b->coefs.assign(reinterpret_cast<unsigned char *>(&cf), reinterpret_cast<unsigned char *>(&cf) + sizeof cf);
+}
+
+void drop_graph(dugks_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+// descriptors and work list of all used slots (waits for the stream first)
+template <typename T, typename ST>
+int rebuild_t(dugks_batch *b) {
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch synchronize");
+    drop_graph(b);
+    const FastGeom g = Launch<T, ST>::fast_geom(b->variant);
+    const int n = (int)b->slots.size();
+    if (n > b->grids_cap) {
+        const int cap = std::max(16, n * 2);
+        void *grids = nullptr;
+        double *mass = nullptr;
+        if (cudaMalloc(&grids, (size_t)cap * sizeof(BatchGrid<T>)) != cudaSuccess ||
+            cudaMalloc(&mass, (size_t)cap * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            if (grids) cudaFree(grids);
+            return bfail(b, DUGKS_ENOMEM, "batch descriptors");
+        }
+        cudaMemset(mass, 0, (size_t)cap * sizeof(double));
+        if (b->d_mass) cudaMemcpy(mass, b->d_mass, (size_t)b->grids_cap * sizeof(double), cudaMemcpyDeviceToDevice);
+        if (b->d_grids) cudaFree(b->d_grids);
+        if (b->d_mass) cudaFree(b->d_mass);
+        b->d_grids = grids;
+        b->d_mass = mass;
+        b->grids_cap = cap;
+    }
+    b->h_grids.assign((size_t)std::max(n, 1) * sizeof(BatchGrid<T>), 0);
+    b->h_items.clear();
+    BatchGrid<T> *G = reinterpret_cast<BatchGrid<T> *>(b->h_grids.data());
+    const bool half = Store<T, ST>::deviation;
+    for (int i = 0; i < n; i++) {
+        const Slot &s = b->slots[i];
+        BatchGrid<T> &d = G[i];
+        std::memset(&d, 0, sizeof d);
+        if (!s.used) {
+            d.step = 0;
+            d.target = 0;   // frozen
+            continue;
+        }
+        for (int k = 0; k < 2; k++) {
+            d.X[k] = s.X[k];
+            if (!encode_plane_map(&d.tmX[k], s.X[k], sizeof(ST), half, s.pitch, s.ny, s.plane, 9, g.box_w, g.box_h))
+                return bfail(b, DUGKS_ECUDA, "tensor map encoding failed");
+        }
+        for (int k = 0; k < b->nphi; k++) {
+            d.phi[k] = static_cast<T *>(s.phi[k]);
+            if (!encode_plane_map(&d.tmPhi[k], s.phi[k], sizeof(T), false, s.pitch, s.ny, s.plane, 1, g.box_wt,
+                                  g.box_h))
+                return bfail(b, DUGKS_ECUDA, "tensor map encoding failed");
+        }
+        if (b->nphi == 2) d.tmPhi[2] = d.tmPhi[0];
+        d.step = s.step;
+        d.target = s.target < 0 ? (long long)1 << 62 : s.target;
+        d.plane = s.plane;
+        d.nx = s.nx;
+        d.ny = s.ny;
+        d.pitch = s.pitch;
+        d.tiles_x = s.tiles_x;
+        d.item0 = (int)b->h_items.size();
+        d.nitems = s.tiles_x * s.tiles_y;
+        d.vel_kind = s.vel_kind;
+        for (int k = 0; k < 3; k++) d.vp[k] = s.vel[k];
+        for (int by = 0; by < s.tiles_y; by++)
+            for (int bx = 0; bx < s.tiles_x; bx++) b->h_items.push_back(make_int4(i, bx, by, 0));
+    }
+    b->nitems = (int)b->h_items.size();
+    if (b->nitems > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        if (b->d_partials) cudaFree(b->d_partials);
+        b->d_items = nullptr;
+        b->d_partials = nullptr;
+        b->items_cap = 0;
+        const int cap = b->nitems * 2;
+        if (cudaMalloc(&b->d_items, (size_t)cap * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc(&b->d_partials, (size_t)cap * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, DUGKS_ENOMEM, "batch work list");
+        }
+        b->items_cap = cap;
+    }
+    if (n > 0) e = cudaMemcpy(b->d_grids, b->h_grids.data(), (size_t)n * sizeof(BatchGrid<T>), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b->nitems > 0)
+        e = cudaMemcpy(b->d_items, b->h_items.data(), (size_t)b->nitems * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(b, e, "batch descriptors upload");
+    b->dirty = false;
+    return DUGKS_OK;
+}
+
+int rebuild(dugks_batch *b) {
+    switch (b->p.precision) {
+    case DUGKS_FP64: return rebuild_t<double, double>(b);
+    case DUGKS_FP32: return rebuild_t<float, float>(b);
+    default: return rebuild_t<float, __half>(b);
+    }
+}
+
+template <typename T, typename ST>
+cudaError_t launch_one_step(dugks_batch *b) {
+    const BatchUniform<T> &u = *reinterpret_cast<const BatchUniform<T> *>(b->uniform.data());
+    const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(b->coefs.data());
+    BatchGrid<T> *G = static_cast<BatchGrid<T> *>(b->d_grids);
+    cudaError_t e = Launch<T, ST>::batch_step(u, cf, G, b->d_items, b->nitems, b->d_partials, b->p.order, b->p.flux,
+                                              b->variant, b->ctas, b->stream);
+    if (e != cudaSuccess) return e;
+    return launch_batch_advance<T>(G, (int)b->slots.size(), b->d_partials, b->d_mass, b->d_status, b->stream);
+}
+
+cudaError_t one_step(dugks_batch *b) {
+    switch (b->p.precision) {
+    case DUGKS_FP64: return launch_one_step<double, double>(b);
+    case DUGKS_FP32: return launch_one_step<float, float>(b);
+    default: return launch_one_step<float, __half>(b);
+    }
+}
+
+template <typename T, typename ST>
+StepParams<T> slot_view(const dugks_batch *b, const Slot &s) {
+    StepParams<T> q;
+    std::memset(&q, 0, sizeof q);
+    q.nx = s.nx;
+    q.ny = s.ny;
+    q.pitch = s.pitch;
+    q.plane = s.plane;
+    q.status = b->d_status;
+    q.theta_c = (T)(-4.0 / (b->p.W * (b->p.phiA - b->p.phiB)));
+    q.phiA = (T)b->p.phiA;
+    q.phiB = (T)b->p.phiB;
+    q.vel_kind = s.vel_kind;
+    q.vp0 = (T)s.vel[0];
+    q.vp1 = (T)s.vel[1];
+    q.vp2 = (T)s.vel[2];
+    q.qscale = (T)256.0;
+    q.qinv = (T)(1.0 / 256.0);
+    q.X = s.X[s.step & 1];
+    if (Store<T, ST>::deviation) q.phi_cur = static_cast<const T *>(s.phi[(3 - (int)(s.step % 3)) % 3]);
+    q.tile_w = TILE_X;
+    q.tile_h = TILE_Y;
+    q.tiles_x = (s.nx + TILE_X - 1) / TILE_X;
+    return q;
+}
+
+template <typename T, typename ST>
+int init_slot(dugks_batch *b, Slot &s, const double *phi0) {
+    void *d_phi0 = nullptr;
+    if (cudaMalloc(&d_phi0, s.plane * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return DUGKS_ENOMEM;
+    }
+    cudaError_t e = upload_ghosted_plane(d_phi0, phi0, s.nx, s.ny, s.pitch, sizeof(T) == 8);
+    if (e == cudaSuccess) {
+        StepParams<T> q = slot_view<T, ST>(b, s);
+        q.t = (T)0;
+        q.out1 = s.X[0];
+        q.phi_out = static_cast<T *>(s.phi[0]);
+        e = Launch<T, ST>::init(q, static_cast<const T *>(d_phi0), (T)(0.5 * b->p.cfl), b->p.order, b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaFree(d_phi0);
+    return e == cudaSuccess ? DUGKS_OK : bcuda(b, e, "batch init");
+}
+
+void free_slot(Slot &s) {
+    for (void *q : {s.X[0], s.X[1], s.phi[0], s.phi[1], s.phi[2]})
+        if (q) cudaFree(q);
+    s = Slot();
+}
+
+int check_common(const dugks_params *p) {
+    if (!p) return DUGKS_EINVAL;
+    if (!(p->W > 0) || !(p->M > 0) || !(p->cfl > 0) || p->cfl > 1.0) return DUGKS_EINVAL;
+    if ((p->order != 2 && p->order != 3) || (p->flux != 0 && p->flux != 1) || p->stages != 2) return DUGKS_EINVAL;
+    if (p->precision < DUGKS_FP64 || p->precision > DUGKS_FP16F) return DUGKS_EINVAL;
+    if (!(p->phiA != p->phiB)) return DUGKS_EINVAL;
+    return DUGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dugks_batch_create(const dugks_params *common, void *cuda_stream, dugks_batch **out) {
+    if (!out) return DUGKS_EINVAL;
+    *out = nullptr;
+    int r = check_common(common);
+    if (r != DUGKS_OK) return r;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return DUGKS_ECUDA;
+    }
+    if (!encode_fn()) return DUGKS_ECUDA;
+    dugks_batch *b = new dugks_batch();
+    b->p = *common;
+    cudaGetDevice(&b->dev);
+    if (cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        b->own_stream = true;
+    } else {
+        delete b;
+        return DUGKS_ECUDA;
+    }
+    b->tsize = fp64(b) ? 8 : 4;
+    b->ssize = common->precision == DUGKS_FP64 ? 8 : common->precision == DUGKS_FP32 ? 4 : 2;
+    b->nphi = common->precision == DUGKS_FP16F ? 3 : 2;
+    if (const char *ev = std::getenv("DUGKS_FAST_VARIANT")) {
+        const int v = std::atoi(ev);
+        if (v >= 0 && v < FAST_VARIANTS) b->variant = v;
+    }
+    if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        dugks_batch_destroy(b);
+        return DUGKS_ENOMEM;
+    }
+    cudaMemset(b->d_status, 0, sizeof(int));
+    b->ctas = resident_ctas(b);
+    if (fp64(b)) fill_uniform<double>(b, batch_geom(b));
+    else fill_uniform<float>(b, batch_geom(b));
+    *out = b;
+    return DUGKS_OK;
+}
+
+size_t dugks_batch_grid_bytes(const dugks_params *common, int32_t nx, int32_t ny) {
+    if (!common || nx < 8 || ny < 8) return 0;
+    const size_t plane = plane_of(nx, ny, nullptr);
+    const size_t ts = common->precision == DUGKS_FP64 ? 8 : 4;
+    const size_t ss = common->precision == DUGKS_FP64 ? 8 : common->precision == DUGKS_FP32 ? 4 : 2;
+    const int nphi = common->precision == DUGKS_FP16F ? 3 : 2;
+    return 2 * 9 * plane * ss + (size_t)nphi * plane * ts;
+}
+
+int dugks_batch_add(dugks_batch *b, int32_t nx, int32_t ny, const double *phi0_host, int vel_kind,
+                    const double *vel_params, int64_t target_steps, int32_t *grid_id) {
+    if (!b || !phi0_host || !grid_id || nx < 8 || ny < 8) return DUGKS_EINVAL;
+    if (b->sticky != DUGKS_OK) return b->sticky;
+    if (vel_kind != DUGKS_VEL_UNIFORM && vel_kind != DUGKS_VEL_ROTATION && vel_kind != DUGKS_VEL_VORTEX)
+        return bfail(b, DUGKS_EINVAL, "batch grids take uniform, rotation or vortex velocity");
+    if (!vel_params) return bfail(b, DUGKS_EINVAL, "velocity parameters missing");
+    if (vel_kind == DUGKS_VEL_VORTEX && (!(vel_params[0] > 0) || !(vel_params[2] > 0)))
+        return bfail(b, DUGKS_EINVAL, "vortex needs (L > 0, U, T > 0)");
+    for (size_t i = 0; i < (size_t)nx * ny; i++)
+        if (!std::isfinite(phi0_host[i])) return DUGKS_ENONFINITE;
+    cudaSetDevice(b->dev);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch synchronize");
+    Slot s;
+    s.used = true;
+    s.nx = nx;
+    s.ny = ny;
+    s.plane = plane_of(nx, ny, &s.pitch);
+    const FastGeom g = batch_geom(b);
+    s.tiles_x = (nx + g.tile_w - 1) / g.tile_w;
+    s.tiles_y = (ny + g.tile_h - 1) / g.tile_h;
+    s.vel_kind = vel_kind;
+    const int nv = vel_kind == DUGKS_VEL_UNIFORM ? 2 : 3;
+    for (int k = 0; k < nv; k++) s.vel[k] = vel_params[k];
+    s.target = target_steps;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; k++) ok = cudaMalloc(&s.X[k], 9 * s.plane * b->ssize) == cudaSuccess;
+    for (int k = 0; k < b->nphi && ok; k++) ok = cudaMalloc(&s.phi[k], s.plane * b->tsize) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_slot(s);
+        return DUGKS_ENOMEM;   // not sticky: the caller may retry later
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMemset(s.X[k], 0, 9 * s.plane * b->ssize);
+    for (int k = 0; k < b->nphi && e == cudaSuccess; k++) e = cudaMemset(s.phi[k], 0, s.plane * b->tsize);
+    if (e != cudaSuccess) {
+        free_slot(s);
+        return bcuda(b, e, "batch grid clear");
+    }
+    int r;
+    switch (b->p.precision) {
+    case DUGKS_FP64: r = init_slot<double, double>(b, s, phi0_host); break;
+    case DUGKS_FP32: r = init_slot<float, float>(b, s, phi0_host); break;
+    default: r = init_slot<float, __half>(b, s, phi0_host); break;
+    }
+    if (r != DUGKS_OK) {
+        free_slot(s);
+        return r;
+    }
+    int id = -1;
+    for (size_t i = 0; i < b->slots.size(); i++)
+        if (!b->slots[i].used) {
+            id = (int)i;
+            break;
+        }
+    if (id < 0) {
+        id = (int)b->slots.size();
+        b->slots.push_back(Slot());
+    }
+    b->slots[id] = s;
+    b->dirty = true;
+    *grid_id = id;
+    return DUGKS_OK;
+}
+
+int dugks_batch_remove(dugks_batch *b, int32_t grid_id) {
+    if (!b || grid_id < 0 || grid_id >= (int)b->slots.size() || !b->slots[grid_id].used) return DUGKS_EINVAL;
+    cudaSetDevice(b->dev);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch synchronize");
+    free_slot(b->slots[grid_id]);
+    b->dirty = true;
+    return DUGKS_OK;
+}
+
+int dugks_batch_step(dugks_batch *b, int64_t nsteps) {
+    if (!b || nsteps < 0) return DUGKS_EINVAL;
+    if (b->sticky != DUGKS_OK) return b->sticky;
+    cudaSetDevice(b->dev);
+    if (b->dirty) {
+        int r = rebuild(b);
+        if (r != DUGKS_OK) return r;
+    }
+    int64_t left = nsteps;
+    cudaError_t e = cudaSuccess;
+    while (left > 0 && e == cudaSuccess) {
+        if (left >= GRAPH_STEPS) {
+            if (!b->graph) {   // capture GRAPH_STEPS steps once; replayed while the work list is unchanged
+                cudaGraph_t g = nullptr;
+                e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+                for (int i = 0; i < GRAPH_STEPS && e == cudaSuccess; i++) e = one_step(b);
+                cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+                if (e == cudaSuccess) e = e2;
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e != cudaSuccess) break;
+            }
+            e = cudaGraphLaunch(b->graph, b->stream);
+            left -= GRAPH_STEPS;
+            for (auto &s : b->slots)
+                if (s.used) s.step = s.target < 0 ? s.step + GRAPH_STEPS : std::min(s.target, s.step + GRAPH_STEPS);
+        } else {
+            e = one_step(b);
+            left -= 1;
+            for (auto &s : b->slots)
+                if (s.used && (s.target < 0 || s.step < s.target)) s.step += 1;
+        }
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "batch step");
+    for (auto &s : b->slots)
+        if (s.used && s.step > 0) s.mass_known = true;
+    return DUGKS_OK;
+}
+
+int64_t dugks_batch_step_index(const dugks_batch *b, int32_t grid_id) {
+    if (!b || grid_id < 0 || grid_id >= (int)b->slots.size() || !b->slots[grid_id].used) return -1;
+    return b->slots[grid_id].step;
+}
+
+int64_t dugks_batch_active_cells(const dugks_batch *b) {
+    if (!b) return 0;
+    int64_t n = 0;
+    for (auto &s : b->slots)
+        if (s.used && (s.target < 0 || s.step < s.target)) n += (int64_t)s.nx * s.ny;
+    return n;
+}
+
+int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host) {
+    if (!b || !out_host || grid_id < 0 || grid_id >= (int)b->slots.size() || !b->slots[grid_id].used)
+        return DUGKS_EINVAL;
+    if (b->sticky != DUGKS_OK) return b->sticky;
+    cudaSetDevice(b->dev);
+    const Slot &s = b->slots[grid_id];
+    const size_t n = (size_t)s.nx * s.ny, bytes = n * b->tsize;
+    if (bytes > b->tmp_bytes) {
+        cudaStreamSynchronize(b->stream);
+        if (b->d_tmp) cudaFree(b->d_tmp);
+        b->d_tmp = nullptr;
+        b->tmp_bytes = 0;
+        if (cudaMalloc(&b->d_tmp, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, DUGKS_ENOMEM, "read-out buffer");
+        }
+        b->tmp_bytes = bytes;
+    }
+    cudaError_t e;
+    switch (b->p.precision) {
+    case DUGKS_FP64: e = Launch<double, double>::phi(slot_view<double, double>(b, s), static_cast<double *>(b->d_tmp), b->stream); break;
+    case DUGKS_FP32: e = Launch<float, float>::phi(slot_view<float, float>(b, s), static_cast<float *>(b->d_tmp), b->stream); break;
+    default: e = Launch<float, __half>::phi(slot_view<float, __half>(b, s), static_cast<float *>(b->d_tmp), b->stream); break;
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "phi kernel");
+    if (fp64(b)) {
+        e = cudaMemcpyAsync(out_host, b->d_tmp, bytes, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    } else {
+        std::vector<float> tmp(n);
+        e = cudaMemcpyAsync(tmp.data(), b->d_tmp, bytes, cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        for (size_t i = 0; i < n && e == cudaSuccess; i++) out_host[i] = tmp[i];
+    }
+    return e == cudaSuccess ? b->sticky : bcuda(b, e, "read phi");
+}
+
+int dugks_batch_mass(dugks_batch *b, int32_t grid_id, double *out) {
+    if (!b || !out || grid_id < 0 || grid_id >= (int)b->slots.size() || !b->slots[grid_id].used) return DUGKS_EINVAL;
+    if (b->sticky != DUGKS_OK) return b->sticky;
+    cudaSetDevice(b->dev);
+    const Slot &s = b->slots[grid_id];
+    cudaError_t e;
+    if (s.mass_known && b->d_mass) {
+        e = cudaMemcpyAsync(out, b->d_mass + grid_id, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    } else {
+        // before the first step: reduce the initial state with the generic tiling
+        const int tiles = ((s.nx + TILE_X - 1) / TILE_X) * ((s.ny + TILE_Y - 1) / TILE_Y);
+        const size_t need = (size_t)tiles * sizeof(double) + sizeof(double);
+        if (need > b->tmp_bytes) {
+            cudaStreamSynchronize(b->stream);
+            if (b->d_tmp) cudaFree(b->d_tmp);
+            b->d_tmp = nullptr;
+            b->tmp_bytes = 0;
+            if (cudaMalloc(&b->d_tmp, need) != cudaSuccess) {
+                cudaGetLastError();
+                return bfail(b, DUGKS_ENOMEM, "mass buffer");
+            }
+            b->tmp_bytes = need;
+        }
+        double *part = static_cast<double *>(b->d_tmp), *res = part + tiles;
+        switch (b->p.precision) {
+        case DUGKS_FP64: { auto q = slot_view<double, double>(b, s); q.mass_partial = part; e = Launch<double, double>::mass_partial(q, b->stream); break; }
+        case DUGKS_FP32: { auto q = slot_view<float, float>(b, s); q.mass_partial = part; e = Launch<float, float>::mass_partial(q, b->stream); break; }
+        default: { auto q = slot_view<float, __half>(b, s); q.mass_partial = part; e = Launch<float, __half>::mass_partial(q, b->stream); break; }
+        }
+        if (e == cudaSuccess) e = launch_mass_final(part, tiles, res, b->d_status, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch mass");
+    if (!std::isfinite(*out)) return bfail(b, DUGKS_ENONFINITE, "the field holds NaN or Inf");
+    return DUGKS_OK;
+}
+
+int dugks_batch_set_variant(dugks_batch *b, int variant) {
+    if (!b || variant < 0 || variant >= FAST_VARIANTS) return DUGKS_EINVAL;
+    cudaSetDevice(b->dev);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch synchronize");
+    b->variant = variant;
+    b->ctas = resident_ctas(b);
+    const FastGeom g = batch_geom(b);
+    if (fp64(b)) fill_uniform<double>(b, g);
+    else fill_uniform<float>(b, g);
+    for (auto &s : b->slots)
+        if (s.used) {
+            s.tiles_x = (s.nx + g.tile_w - 1) / g.tile_w;
+            s.tiles_y = (s.ny + g.tile_h - 1) / g.tile_h;
+        }
+    b->dirty = true;
+    return DUGKS_OK;
+}
+
+int dugks_batch_status(dugks_batch *b) {
+    if (!b) return DUGKS_EINVAL;
+    cudaSetDevice(b->dev);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch synchronize");
+    int flags = 0;
+    e = cudaMemcpy(&flags, b->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "read status");
+    if (flags & 2) return bfail(b, DUGKS_ETIMEOUT, "a device wait ran out");
+    if (flags & 1) return bfail(b, DUGKS_ENONFINITE, "a grid holds NaN or Inf");
+    return b->sticky;
+}
+
+const char *dugks_batch_last_error(const dugks_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+void dugks_batch_destroy(dugks_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->dev);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    for (auto &s : b->slots) free_slot(s);
+    for (void *q : {b->d_grids, (void *)b->d_items, (void *)b->d_partials, (void *)b->d_mass, (void *)b->d_status, b->d_tmp})
+        if (q) cudaFree(q);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // extern "C"

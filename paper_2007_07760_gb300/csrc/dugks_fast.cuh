@@ -188,8 +188,7 @@ struct FastTile {
     static constexpr size_t oF = al(oV + sizeof(T) * 2 * NC);
     static constexpr size_t oNB = al(oF + sizeof(T) * 2 * NC);
     static constexpr size_t oQ = al(oNB + sizeof(T) * 2 * NW * 32);
-    static constexpr size_t oCoef = al(oQ + sizeof(T) * 3 * NW * 32);
-    static constexpr size_t oVel = al(oCoef + sizeof(T) * (9 * 12 + 9 * 16 + 9 * 4));
+    static constexpr size_t oVel = al(oQ + sizeof(T) * 3 * NW * 32);
     static constexpr size_t oRed = al(oVel + sizeof(T) * 4 * (CW + CH));
     static constexpr size_t oBar = oRed + sizeof(double) * 32;
     static constexpr size_t smem_bytes = oBar + 16;
@@ -197,18 +196,21 @@ struct FastTile {
         (uint32_t)(sizeof(ST) * 9 * BW * RH + sizeof(T) * BWT * RH * (DEV ? 2 : 1));
 };
 
+// One tile (bx, by) of one grid. The caller initialised the mbarrier `bar`
+// (count 1) and passes the parity of its next phase. Returns false if the TMA
+// copy never arrived (status flagged). mass_out: where the tile's FP64 partial
+// goes (may be null).
 template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
-__global__ void __launch_bounds__(NW * 32)
-step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant__ FaceCoefs<T> cf,
-                 const __grid_constant__ FastExtra<T> fe_, const __grid_constant__ CUtensorMap tmX,
-                 const __grid_constant__ CUtensorMap tmPo, const __grid_constant__ CUtensorMap tmPc) {
+__device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe_,
+                                          const CUtensorMap *tmX, const CUtensorMap *tmPo, const CUtensorMap *tmPc,
+                                          int bx, int by, double *mass_out, unsigned char *smem, uint64_t *bar,
+                                          uint32_t phase) {
     using FT = FastTile<T, ST, NW, MR>;
     constexpr int TX = FT::TX, TY = FT::TY, RW = FT::RW, CW = FT::CW, CH = FT::CH, NC = FT::NC;
     constexpr int NT = FT::NT, BW = FT::BW, BWT = FT::BWT, RH = FT::RH, NE = FT::NE, NXS = FT::NXS;
     constexpr bool DEV = FT::DEV;
     static_assert(ORDER == 2 || ORDER == 3, "fast path covers orders 2 and 3");
 
-    extern __shared__ __align__(128) unsigned char smem[];
     ST *sX = reinterpret_cast<ST *>(smem + FT::oX);
     T *sPo = reinterpret_cast<T *>(smem + FT::oPo);
     T *sPc = reinterpret_cast<T *>(smem + FT::oPc);
@@ -218,39 +220,29 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
     T *sF = reinterpret_cast<T *>(smem + FT::oF);
     T *sNB = reinterpret_cast<T *>(smem + FT::oNB);
     T *sQ = reinterpret_cast<T *>(smem + FT::oQ);
-    T *sCE = reinterpret_cast<T *>(smem + FT::oCoef);   // [9][3][4]
-    T *sCN = sCE + 9 * 12;                              // [9][4][4]
-    T *sK = sCN + 9 * 16;                               // [9][4]: xi_x, xi_y, w, 0
     T *sVel = reinterpret_cast<T *>(smem + FT::oVel);   // vortex factors, see below
     double *sred = reinterpret_cast<double *>(smem + FT::oRed);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + FT::oBar);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = p.nx, ny = p.ny;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     // padded-plane coordinates of the state box; ox = offset of relative x = -3 in the box
     const int xs_raw = x0 - 3 + GHOST, ys = y0 - 3 + GHOST;
     const int xs = xs_raw / FT::AS * FT::AS, ox = xs_raw - xs;
     const int xst = xs_raw / FT::AT * FT::AT, oxt = xs_raw - xst;
 
     // ---- S0: one TMA box for the 9 planes (+ phi planes) --------------------
-    if (tid == 0) mbar_init(bar, 1);
+    // (the barrier also orders this tile's copy after the previous tile's
+    // shared-memory accesses when a CTA processes several tiles)
     __syncthreads();
     if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, FT::tx_bytes);
-        tma_load_3d(sX, &tmX, xs, ys, 0, bar);
-        tma_load_2d(sPo, &tmPo, xst, ys, bar);
-        if constexpr (DEV) tma_load_2d(sPc, &tmPc, xst, ys, bar);
+        tma_load_3d(sX, tmX, xs, ys, 0, bar);
+        tma_load_2d(sPo, tmPo, xst, ys, bar);
+        if constexpr (DEV) tma_load_2d(sPc, tmPc, xst, ys, bar);
     }
-    // while the copy is in flight: tables of face coefficients, lattice, velocity
-    for (int i = tid; i < 9 * 12; i += NT) sCE[i] = (&cf.e[0][0][0])[i];
-    for (int i = tid; i < 9 * 16; i += NT) sCN[i] = (&cf.n[0][0][0])[i];
-    if (tid < 9) {
-        sK[tid * 4 + 0] = T(ex(tid));
-        sK[tid * 4 + 1] = T(ey(tid));
-        sK[tid * 4 + 2] = wq<T>(tid);
-        sK[tid * 4 + 3] = T(0);
-    }
+    // while the copy is in flight: velocity tables
     // single vortex u = -U A(x) B(y) c(t), v = U A(y) B(x) c(t), with
     // A(s) = sin^2(pi s / L), B(s) = sin(2 pi s / L) at cell centres (s = i + 1/2)
     // and at faces (s = i + 1) of the wrapped cells of this tile (+2 halo)
@@ -275,12 +267,12 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
             }
         }
     }
-    if (!mbar_wait_bounded(bar, 0, MBAR_MAX_POLLS)) {
+    if (!mbar_wait_bounded(bar, phase, MBAR_MAX_POLLS)) {
         // the copy never completed: flag it, give it one more bounded chance to
         // land (it targets this CTA's shared memory), and leave
         if (tid == 0) atomicOr(p.status, 2);
-        mbar_wait_bounded(bar, 0, MBAR_MAX_POLLS);
-        return;
+        mbar_wait_bounded(bar, phase, MBAR_MAX_POLLS);
+        return false;
     }
 
     // accessors (relative cell coordinates x, y of the tile)
@@ -576,9 +568,167 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
         }
         msum += (double)phn;
     }
-    if (p.mass_partial != nullptr) {
+    if (mass_out != nullptr) {
         const double s = block_sum(msum, sred);
-        if (tid == 0) p.mass_partial[blockIdx.y * p.tiles_x + blockIdx.x] = s;
+        if (tid == 0) *mass_out = s;
+    }
+    return true;
+}
+
+template <typename T, typename ST, int NW, int MR>
+__device__ __forceinline__ uint64_t *fast_bar(unsigned char *smem) {
+    return reinterpret_cast<uint64_t *>(smem + FastTile<T, ST, NW, MR>::oBar);
+}
+
+// One grid, one tile per CTA.
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
+__global__ void __launch_bounds__(NW * 32)
+step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant__ FaceCoefs<T> cf,
+                 const __grid_constant__ FastExtra<T> fe_, const __grid_constant__ CUtensorMap tmX,
+                 const __grid_constant__ CUtensorMap tmPo, const __grid_constant__ CUtensorMap tmPc) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = fast_bar<T, ST, NW, MR>(smem);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    double *mo = p.mass_partial ? p.mass_partial + blockIdx.y * p.tiles_x + blockIdx.x : nullptr;
+    fast_tile<T, ST, ORDER, FLUX, NW, MR>(p, cf, fe_, &tmX, &tmPo, &tmPc, blockIdx.x, blockIdx.y, mo, smem, bar, 0);
+}
+
+// ---- many grids per launch ----------------------------------------------------
+// Per-grid descriptor of a batch, in device memory. The tensor maps are read by
+// TMA from global memory. `step` counts the grid's steps; it selects the
+// ping-pong state set and the phi plane roles, and it is advanced by
+// batch_advance_kernel, so a captured sequence of launches stays valid while
+// grids join and leave (their step counters differ).
+template <typename T>
+struct alignas(64) BatchGrid {
+    CUtensorMap tmX[2];      // state sets 0, 1
+    CUtensorMap tmPhi[3];    // phi planes
+    void *X[2];
+    T *phi[3];
+    long long step, target;  // steps taken; the grid is frozen once step == target
+    size_t plane;
+    int nx, ny, pitch, tiles_x;
+    int item0, nitems;       // its tiles in the work list
+    int vel_kind, pad_;
+    double vp[3];            // velocity parameters (FP64; rounded per precision in the kernel)
+};
+
+// Parameters common to every grid of a batch (same W, M, cfl, order, flux, precision).
+template <typename T>
+struct BatchUniform {
+    T b, h, c1, c2, c3, be1, ga1, tau, theta_c, phiA, phiB, inv_dt, qscale, qinv;
+    double dt;
+    int dtphiu, tile_w, tile_h;
+    int *status;
+};
+
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
+__global__ void __launch_bounds__(NW * 32)
+batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_constant__ FaceCoefs<T> cf,
+                  const BatchGrid<T> *__restrict__ grids, const int4 *__restrict__ items, int nitems,
+                  double *__restrict__ partials) {
+    constexpr bool DEV = Store<T, ST>::deviation;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = fast_bar<T, ST, NW, MR>(smem);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    uint32_t phase = 0;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int4 w = items[it];
+        const BatchGrid<T> *G = grids + w.x;
+        const long long step = G->step;
+        if (step >= G->target) continue;   // frozen grid (uniform for the CTA)
+        StepParams<T> p;
+        p.nx = G->nx;
+        p.ny = G->ny;
+        p.pitch = G->pitch;
+        p.plane = G->plane;
+        p.status = u.status;
+        p.tiles_x = G->tiles_x;
+        p.tile_w = u.tile_w;
+        p.tile_h = u.tile_h;
+        p.acc = nullptr;
+        p.out2 = nullptr;
+        p.mass_partial = nullptr;
+        p.ufield = p.vfield = nullptr;
+        p.a = T(1) - u.b;
+        p.b = u.b;
+        p.h = u.h;
+        p.c1 = u.c1;
+        p.c2 = u.c2;
+        p.c3 = u.c3;
+        p.al1 = T(1) - u.be1;
+        p.be1 = u.be1;
+        p.ga1 = u.ga1;
+        p.al2 = p.be2 = p.ga2 = T(0);
+        p.tau = u.tau;
+        p.theta_c = u.theta_c;
+        p.phiA = u.phiA;
+        p.phiB = u.phiB;
+        p.inv_dtD = u.inv_dt;
+        p.useD = (u.dtphiu && step > 0) ? 1 : 0;
+        p.vel_kind = G->vel_kind;
+        p.vp0 = (T)G->vp[0];
+        p.vp1 = (T)G->vp[1];
+        p.vp2 = (T)G->vp[2];
+        const double t = (double)step * u.dt;
+        p.t = (T)t;
+        p.t_old = (T)(t - u.dt);
+        p.t_face = (T)(t + 0.5 * u.dt);
+        p.qscale = u.qscale;
+        p.qinv = u.qinv;
+        FastExtra<T> fe;
+        fe.vc_t = fe.vc_told = fe.vc_tface = T(0);
+        if (G->vel_kind == VEL_VORTEX) {
+            const double Tp = G->vp[2];
+            fe.vc_t = (T)cospi(t / Tp);
+            fe.vc_told = (T)cospi((t - u.dt) / Tp);
+            fe.vc_tface = (T)cospi((t + 0.5 * u.dt) / Tp);
+        }
+        const int cur = (int)(step & 1);
+        p.X = G->X[cur];
+        p.out1 = G->X[1 - cur];
+        int iPc = 0, iPo, iOut;
+        if constexpr (DEV) {   // roles rotate with period 3 (see the context API)
+            iPc = (3 - (int)(step % 3)) % 3;
+            iPo = (iPc + 1) % 3;
+            iOut = (iPc + 2) % 3;
+            p.phi_cur = G->phi[iPc];
+        } else {
+            iPo = cur;
+            iOut = 1 - cur;
+            p.phi_cur = nullptr;
+        }
+        p.phi_old = G->phi[iPo];
+        p.phi_out = G->phi[iOut];
+        if (threadIdx.x == 0) {
+            // tensor maps written to global memory by the host: order them for the TMA unit
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmX[cur]) : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmPhi[iPo]) : "memory");
+            if constexpr (DEV)
+                asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmPhi[iPc]) : "memory");
+        }
+        if (!fast_tile<T, ST, ORDER, FLUX, NW, MR>(p, cf, fe, &G->tmX[cur], &G->tmPhi[iPo], &G->tmPhi[iPc], w.y, w.z,
+                                                  partials + it, smem, bar, phase))
+            return;
+        phase ^= 1u;
+    }
+}
+
+// After a batch step: per-grid FP64 mass (fixed-order sum of its tile partials)
+// and the step counter. One CTA per grid.
+template <typename T>
+__global__ void __launch_bounds__(256)
+batch_advance_kernel(BatchGrid<T> *grids, const double *partials, double *mass, int *status) {
+    __shared__ double sred[32];
+    BatchGrid<T> *G = grids + blockIdx.x;
+    if (G->step >= G->target) return;   // uniform for the CTA
+    double s = 0.0;
+    for (int i = threadIdx.x; i < G->nitems; i += blockDim.x) s += partials[G->item0 + i];
+    s = block_sum(s, sred);
+    if (threadIdx.x == 0) {
+        mass[blockIdx.x] = s;
+        if (!isfinite(s)) atomicOr(status, 1);
+        G->step = G->step + 1;
     }
 }
 

@@ -1,0 +1,144 @@
+// dugks_host.h -- host helpers shared by the context API (dugks_api.cu) and the
+// batch API (dugks_batch.cu): face-stencil coefficients of the fast kernel, TMA
+// tensor maps of the ghost-bordered plane layout, and ghosted uploads.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/dugks.h"
+#include "dugks_internal.h"
+
+namespace dugks {
+namespace host {
+
+// ---- face stencils of the fast path ------------------------------------------
+// The face value bar f_k(x_b) is a fixed linear combination of bar f^+_k at the
+// cells around the face: the Taylor expansion of Eq. (26) (value + d.grad
+// + d d : H / 2 with the 9-point lattice-moment gradient and Hessian) about the
+// upwind cell, or the central form of Eq. (25). Weights at (a, b) of the
+// 3 x 3 block around the expansion cell:
+inline double G9x(int a, int b) { return a * (b == 0 ? 1.0 / 3.0 : 1.0 / 12.0); }
+inline double G9y(int a, int b) { return b * (a == 0 ? 1.0 / 3.0 : 1.0 / 12.0); }
+inline double H9(int i, int j, int a, int b) {   // i, j in {0: x, 1: y}
+    if (i != j) return (a != 0 && b != 0) ? 0.25 * a * b : 0.0;
+    const int along = i == 0 ? a : b, across = i == 0 ? b : a;
+    if (along == 0 && across == 0) return -4.0 / 3.0;
+    if (across == 0) return 2.0 / 3.0;
+    if (along == 0) return -1.0 / 3.0;
+    return 1.0 / 6.0;
+}
+inline double taylor_w(int order, double dx, double dy, int a, int b) {
+    double w = (a == 0 && b == 0) ? 1.0 : 0.0;
+    w += dx * G9x(a, b) + dy * G9y(a, b);
+    if (order >= 3)
+        w += 0.5 * dx * dx * H9(0, 0, a, b) + dx * dy * H9(0, 1, a, b) + 0.5 * dy * dy * H9(1, 1, a, b);
+    return w;
+}
+
+template <typename T>
+inline FaceCoefs<T> make_face_coefs(int order, int flux, double h) {
+    double e[9][3][4] = {}, n[9][4][4] = {};
+    for (int k = 0; k < 9; k++) {
+        const int kx = ex(k), ky = ey(k);
+        // east face: taps (b, a) -> e[k][b + 1][a + 1], b in -1..1, a in -1..2
+        auto addE = [&](int cx, double wgt, double dx, double dy) {   // expansion about cell (cx, 0)
+            for (int b = -1; b <= 1; b++)
+                for (int a = -1; a <= 1; a++) e[k][b + 1][cx + a + 1] += wgt * taylor_w(order, dx, dy, a, b);
+        };
+        auto addN = [&](int cy, double wgt, double dx, double dy) {   // expansion about cell (0, cy)
+            for (int b = -1; b <= 1; b++)
+                for (int a = -1; a <= 1; a++) n[k][cy + b + 1][a + 1] += wgt * taylor_w(order, dx, dy, a, b);
+        };
+        if (flux == DUGKS_UPWIND) {
+            if (kx > 0) addE(0, 1.0, 0.5 - h, -ky * h);
+            else if (kx < 0) addE(1, 1.0, h - 0.5, -ky * h);
+            else { addE(0, 0.5, 0.5, -ky * h); addE(1, 0.5, -0.5, -ky * h); }
+            if (ky > 0) addN(0, 1.0, -kx * h, 0.5 - h);
+            else if (ky < 0) addN(1, 1.0, -kx * h, h - 0.5);
+            else { addN(0, 0.5, -kx * h, 0.5); addN(1, 0.5, -kx * h, -0.5); }
+        } else {
+            // east: (F_c + F_E)/2 - h [xi_x (F_E - F_c) + xi_y (dF/dy(c) + dF/dy(E))/2]
+            e[k][1][1] += 0.5 + h * kx;
+            e[k][1][2] += 0.5 - h * kx;
+            n[k][1][1] += 0.5 + h * ky;
+            n[k][2][1] += 0.5 - h * ky;
+            for (int b = -1; b <= 1; b++)
+                for (int a = -1; a <= 1; a++) {
+                    e[k][b + 1][a + 1] += -0.5 * h * ky * G9y(a, b);
+                    e[k][b + 1][a + 2] += -0.5 * h * ky * G9y(a, b);
+                    n[k][b + 1][a + 1] += -0.5 * h * kx * G9x(a, b);
+                    n[k][b + 2][a + 1] += -0.5 * h * kx * G9x(a, b);
+                }
+        }
+    }
+    FaceCoefs<T> cf;
+    for (int k = 0; k < 9; k++) {
+        for (int b = 0; b < 3; b++)
+            for (int a = 0; a < 4; a++) cf.e[k][b][a] = (T)e[k][b][a];
+        for (int b = 0; b < 4; b++)
+            for (int a = 0; a < 4; a++) cf.n[k][b][a] = (T)n[k][b][a];
+    }
+    return cf;
+}
+
+// ---- TMA tensor maps -----------------------------------------------------------
+inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+inline CUtensorMapDataType tma_type(size_t es, bool half) {
+    if (half) return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    return es == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+}
+
+// planes of `es`-byte elements at base: dims (pitch, ny + 2 GHOST[, nplanes]),
+// box (bw, bh[, nplanes]); the fill of out-of-range elements is zero
+inline bool encode_plane_map(CUtensorMap *m, void *base, size_t es, bool half, int pitch, int ny, size_t plane,
+                             int nplanes, int bw, int bh) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)pitch, (cuuint64_t)(ny + 2 * GHOST), (cuuint64_t)nplanes};
+    const cuuint64_t strides[2] = {(cuuint64_t)pitch * es, (cuuint64_t)plane * es};
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, (cuuint32_t)nplanes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t rank = nplanes > 1 ? 3 : 2;
+    CUresult r = fn(m, tma_type(es, half), rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// host doubles (ny * nx, x fastest) -> device plane (double or float) with the
+// periodic ghost border; synchronous
+inline cudaError_t upload_ghosted_plane(void *dst, const double *src, int nx, int ny, int pitch, bool fp64) {
+    const int G = GHOST, rows = ny + 2 * G;
+    std::vector<double> pad((size_t)rows * pitch, 0.0);
+    for (int y = -G; y < ny + G; y++)
+        for (int x = -G; x < nx + G; x++) {
+            const int sx = ((x % nx) + nx) % nx, sy = ((y % ny) + ny) % ny;
+            pad[(size_t)(y + G) * pitch + (x + G)] = src[(size_t)sy * nx + sx];
+        }
+    if (fp64) return cudaMemcpy(dst, pad.data(), pad.size() * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<float> f(pad.size());
+    for (size_t i = 0; i < f.size(); i++) f[i] = (float)pad[i];
+    return cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+}
+
+}  // namespace host
+}  // namespace dugks

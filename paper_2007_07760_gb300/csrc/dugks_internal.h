@@ -35,10 +35,18 @@ struct Launch {
     static cudaError_t mass_partial(const StepParams<T> &p, cudaStream_t s);
     static cudaError_t phi(const StepParams<T> &p, T *out, cudaStream_t s);
     static FastGeom fast_geom(int variant);
+    static cudaError_t batch_step(const BatchUniform<T> &u, const FaceCoefs<T> &cf, const BatchGrid<T> *grids,
+                                  const int4 *items, int nitems, double *partials, int order, int flux, int variant,
+                                  int ctas, cudaStream_t s);
+    static int batch_ctas_per_sm(int order, int flux, int variant);
     static cudaError_t step_fast(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
                                  const CUtensorMap &tmPo, const CUtensorMap &tmPc, int order, int flux,
                                  int variant, cudaStream_t s);
 };
+
+template <typename T>
+cudaError_t launch_batch_advance(BatchGrid<T> *grids, int ngrids, const double *partials, double *mass, int *status,
+                                 cudaStream_t s);
 
 cudaError_t launch_mass_final(const double *partial, int n, double *out, int *status, cudaStream_t s);
 

@@ -139,4 +139,85 @@ cudaError_t Launch<T, ST>::phi(const StepParams<T> &p, T *out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
+static cudaError_t launch_batch_t(const BatchUniform<T> &u, const FaceCoefs<T> &cf, const BatchGrid<T> *grids,
+                                  const int4 *items, int nitems, double *partials, int ctas, cudaStream_t s) {
+    using FT = FastTile<T, ST, NW, MR>;
+    auto kern = batch_fast_kernel<T, ST, ORDER, FLUX, NW, MR>;
+    // (the shared-memory attribute was set by batch_ctas_per_sm, outside any capture)
+    if (nitems <= 0) return cudaSuccess;
+    kern<<<ctas < nitems ? ctas : nitems, FT::NT, FT::smem_bytes, s>>>(u, cf, grids, items, nitems, partials);
+    return cudaGetLastError();
+}
+
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
+static int batch_occupancy_t() {
+    using FT = FastTile<T, ST, NW, MR>;
+    auto kern = batch_fast_kernel<T, ST, ORDER, FLUX, NW, MR>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FT::smem_bytes);
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, FT::NT, FT::smem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n > 0 ? n : 1;
+}
+
+#define DUGKS_BATCH_DISPATCH(CALL)                                                            \
+    switch (variant) {                                                                        \
+    case 1: return CALL(16, 1);                                                               \
+    case 2: return CALL(8, 2);                                                                \
+    case 3: return CALL(16, 2);                                                               \
+    default: return CALL(8, fast_mr<T>());                                                    \
+    }
+
+template <typename T, typename ST, int ORDER, int FLUX>
+static cudaError_t launch_batch_v(const BatchUniform<T> &u, const FaceCoefs<T> &cf, const BatchGrid<T> *grids,
+                                  const int4 *items, int nitems, double *partials, int variant, int ctas,
+                                  cudaStream_t s) {
+#define CALL(NW, MR) launch_batch_t<T, ST, ORDER, FLUX, NW, MR>(u, cf, grids, items, nitems, partials, ctas, s)
+    DUGKS_BATCH_DISPATCH(CALL)
+#undef CALL
+}
+
+template <typename T, typename ST, int ORDER, int FLUX>
+static int batch_occ_v(int variant) {
+#define CALL(NW, MR) batch_occupancy_t<T, ST, ORDER, FLUX, NW, MR>()
+    DUGKS_BATCH_DISPATCH(CALL)
+#undef CALL
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::batch_step(const BatchUniform<T> &u, const FaceCoefs<T> &cf, const BatchGrid<T> *grids,
+                                      const int4 *items, int nitems, double *partials, int order, int flux,
+                                      int variant, int ctas, cudaStream_t s) {
+    switch (order * 2 + flux) {
+    case 4: return launch_batch_v<T, ST, 2, 0>(u, cf, grids, items, nitems, partials, variant, ctas, s);
+    case 5: return launch_batch_v<T, ST, 2, 1>(u, cf, grids, items, nitems, partials, variant, ctas, s);
+    case 6: return launch_batch_v<T, ST, 3, 0>(u, cf, grids, items, nitems, partials, variant, ctas, s);
+    case 7: return launch_batch_v<T, ST, 3, 1>(u, cf, grids, items, nitems, partials, variant, ctas, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, typename ST>
+int Launch<T, ST>::batch_ctas_per_sm(int order, int flux, int variant) {
+    switch (order * 2 + flux) {
+    case 4: return batch_occ_v<T, ST, 2, 0>(variant);
+    case 5: return batch_occ_v<T, ST, 2, 1>(variant);
+    case 6: return batch_occ_v<T, ST, 3, 0>(variant);
+    case 7: return batch_occ_v<T, ST, 3, 1>(variant);
+    default: return 1;
+    }
+}
+
+template <typename T>
+cudaError_t launch_batch_advance(BatchGrid<T> *grids, int ngrids, const double *partials, double *mass, int *status,
+                                 cudaStream_t s) {
+    if (ngrids <= 0) return cudaSuccess;
+    batch_advance_kernel<T><<<ngrids, 256, 0, s>>>(grids, partials, mass, status);
+    return cudaGetLastError();
+}
+
 }  // namespace dugks

@@ -59,6 +59,20 @@ SIGNATURES = [
     ("dugks_destroy", None, [_VP]),
     ("dugks_field_mass_noalloc", ctypes.c_int,
      [_VP, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP]),
+    ("dugks_batch_create", ctypes.c_int, [ctypes.POINTER(dugks_params), _VP, ctypes.POINTER(_VP)]),
+    ("dugks_batch_grid_bytes", ctypes.c_size_t, [ctypes.POINTER(dugks_params), ctypes.c_int32, ctypes.c_int32]),
+    ("dugks_batch_add", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _DP, ctypes.c_int, _DP, _I64,
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    ("dugks_batch_remove", ctypes.c_int, [_VP, ctypes.c_int32]),
+    ("dugks_batch_step", ctypes.c_int, [_VP, _I64]),
+    ("dugks_batch_step_index", _I64, [_VP, ctypes.c_int32]),
+    ("dugks_batch_read_phi", ctypes.c_int, [_VP, ctypes.c_int32, _DP]),
+    ("dugks_batch_mass", ctypes.c_int, [_VP, ctypes.c_int32, _DP]),
+    ("dugks_batch_set_variant", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("dugks_batch_active_cells", _I64, [_VP]),
+    ("dugks_batch_status", ctypes.c_int, [_VP]),
+    ("dugks_batch_last_error", ctypes.c_char_p, [_VP]),
+    ("dugks_batch_destroy", None, [_VP]),
 ]
 DUGKS_NOALLOC_MAX_TILES = 65536
 
@@ -196,6 +210,144 @@ def make_params(nx, ny, W=4.0, M=0.01, cfl=0.8, order=2, flux=0, stages=2, preci
     p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
     p.dtphiu, p.phiA, p.phiB = dtphiu, phiA, phiB
     return p
+
+
+# ---- batches of grids ----------------------------------------------------------
+
+def _bcheck(b, code: int):
+    if code != DUGKS_OK:
+        msg = lib().dugks_batch_last_error(b).decode() if b else ""
+        raise DugksError(code, msg)
+
+
+def dugks_batch_create(params: dugks_params, stream: int | None = None):
+    out = ctypes.c_void_p()
+    _bcheck(None, lib().dugks_batch_create(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(out)))
+    return out.value
+
+
+def dugks_batch_grid_bytes(params: dugks_params, nx: int, ny: int) -> int:
+    return lib().dugks_batch_grid_bytes(ctypes.byref(params), int(nx), int(ny))
+
+
+def dugks_batch_add(b, nx: int, ny: int, phi0: np.ndarray, vel_kind: int, vel, target_steps: int = -1) -> int:
+    phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+    if phi0.shape != (ny, nx):
+        raise ValueError("phi0 must be (ny, nx)")
+    v = np.ascontiguousarray(list(vel) + [0.0] * 4, dtype=np.float64)
+    gid = ctypes.c_int32()
+    _bcheck(b, lib().dugks_batch_add(b, int(nx), int(ny), _dptr(phi0), int(vel_kind), _dptr(v), int(target_steps),
+                                     ctypes.byref(gid)))
+    return gid.value
+
+
+def dugks_batch_remove(b, gid: int):
+    _bcheck(b, lib().dugks_batch_remove(b, int(gid)))
+
+
+def dugks_batch_step(b, nsteps: int):
+    _bcheck(b, lib().dugks_batch_step(b, int(nsteps)))
+
+
+def dugks_batch_step_index(b, gid: int) -> int:
+    return lib().dugks_batch_step_index(b, int(gid))
+
+
+def dugks_batch_read_phi(b, gid: int, out: np.ndarray):
+    _bcheck(b, lib().dugks_batch_read_phi(b, int(gid), _dptr(out)))
+    return out
+
+
+def dugks_batch_mass(b, gid: int) -> float:
+    m = ctypes.c_double()
+    _bcheck(b, lib().dugks_batch_mass(b, int(gid), ctypes.byref(m)))
+    return m.value
+
+
+def dugks_batch_set_variant(b, variant: int):
+    _bcheck(b, lib().dugks_batch_set_variant(b, int(variant)))
+
+
+def dugks_batch_active_cells(b) -> int:
+    return lib().dugks_batch_active_cells(b)
+
+
+def dugks_batch_status(b) -> int:
+    return lib().dugks_batch_status(b)
+
+
+def dugks_batch_last_error(b) -> str:
+    return lib().dugks_batch_last_error(b).decode()
+
+
+def dugks_batch_destroy(b):
+    if b:
+        lib().dugks_batch_destroy(b)
+
+
+class Batch:
+    """Owning wrapper of a batch of independent grids sharing W, M, cfl, order, flux, precision."""
+
+    def __init__(self, *, stream: int | None = None, **kw):
+        self.params = make_params(8, 8, **kw)
+        self.b = dugks_batch_create(self.params, stream)
+        self.shapes = {}
+
+    def grid_bytes(self, nx: int, ny: int) -> int:
+        return dugks_batch_grid_bytes(self.params, nx, ny)
+
+    def add(self, phi0: np.ndarray, vel_kind="uniform", vel=(0.0, 0.0), target_steps: int = -1) -> int:
+        ny, nx = phi0.shape
+        gid = dugks_batch_add(self.b, nx, ny, phi0, VEL_KINDS[vel_kind], vel, target_steps)
+        self.shapes[gid] = (ny, nx)
+        return gid
+
+    def add_problem(self, prob, target_steps: int | None = None) -> int:
+        return self.add(prob.phi0, prob.vel_kind, prob.vel, prob.steps if target_steps is None else target_steps)
+
+    def remove(self, gid: int):
+        dugks_batch_remove(self.b, gid)
+        self.shapes.pop(gid, None)
+
+    def step(self, n: int = 1):
+        dugks_batch_step(self.b, n)
+        return self
+
+    def step_index(self, gid: int) -> int:
+        return dugks_batch_step_index(self.b, gid)
+
+    def phi(self, gid: int) -> np.ndarray:
+        out = np.empty(self.shapes[gid])
+        return dugks_batch_read_phi(self.b, gid, out)
+
+    def mass(self, gid: int) -> float:
+        return dugks_batch_mass(self.b, gid)
+
+    def set_variant(self, v: int):
+        dugks_batch_set_variant(self.b, v)
+
+    def active_cells(self) -> int:
+        return dugks_batch_active_cells(self.b)
+
+    def status(self) -> int:
+        return dugks_batch_status(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            dugks_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Solver:
