@@ -195,12 +195,20 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
+    if args.workload.startswith("batch"):
+        run_batch(args, dist, world, rank, local)
+        if dist:
+            dist.destroy_process_group()
+        return
     prob, desc = workload(args.workload, args.precision)
     # cpu baseline first (oracle process-local, before heavy GPU use), rank 0, N = 1 only
     cpu = cpu_baseline(prob) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
 
     stream = torch.cuda.Stream()
     solver = N.Solver.from_problem(prob, precision=args.precision, stream=stream.cuda_stream)
+    if args.generic:
+        solver.set_variant(-1)
+        desc["kernel"] = "generic step_kernel (plain comparison path)"
     mass_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -292,7 +300,7 @@ def run_ours(args):
                            replicas=world, parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "step_kernel (fused two-stage DUGKS step)",
+                         "kernel": desc.get("kernel", "step_fast_kernel (TMA-staged fused two-stage DUGKS step)"),
                          "bytes_per_cell": BYTES_PER_CELL[args.precision], "peak_source": peak_kind,
                          "avg_kernel_ms": avg_step_ms},
             "e2e": e2e,
@@ -307,6 +315,128 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args, dist, world, rank, local):
+    """Many independent grids (512, sides log-uniform 64..512, 1-8 drops, uniform
+    velocity |u| <= 0.05) advanced together: one launch per step over a work
+    list of tiles of all grids, replayed as CUDA graphs. The state (2.3 GB in
+    FP32) is far larger than L2, so no flush is needed between steps."""
+    import torch
+    from paper_2007_07760_gb300 import autotune
+    from paper_2007_07760_gb300 import native as N
+
+    count = int(args.workload[len("batch"):] or 512)
+    probs = WL.random_batch(count=count)
+    p0 = probs[0]
+    stream = torch.cuda.Stream()
+    desc = {"workload": f"batch{count}_{args.precision}_p{p0.order}_upwind_2stage", "grids": count,
+            "sides": "log-uniform 64..512 (seeded)", "precision": args.precision, "order": p0.order,
+            "flux": "upwind", "stages": 2, "M": p0.M, "cfl": p0.cfl, "W": p0.W,
+            "velocity": "uniform, random angle, |u| <= 0.05"}
+    cells = sum(q.cells for q in probs)
+    desc["cells"] = cells
+    t_e2e0 = time.perf_counter()
+    batch = N.Batch(precision=args.precision, W=p0.W, M=p0.M, cfl=p0.cfl, order=p0.order, flux=0, stages=2,
+                    stream=stream.cuda_stream)
+    ids = [batch.add(q.phi0, q.vel_kind, q.vel) for q in probs]
+    t_add = time.perf_counter() - t_e2e0
+    variant = autotune.tune(batch, "batch", cells, steps=8, warmup=2)
+    desc["tile_variant"] = variant
+    desc["l2"] = "no flush: the state of all grids is larger than L2"
+    batch.step(args.warmup)
+    batch.status()
+    K = args.steps
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            batch.step(K)
+            ev1.record(stream)
+        stream.synchronize()
+    clocks = clk.summary()
+    total_ms = ev0.elapsed_time(ev1)
+    if batch.status() != 0:
+        raise SystemExit("device error: " + N.dugks_batch_last_error(batch.b))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = cells * K * world / (total_ms * 1e-3)
+    peak, peak_kind = measured_peak_hbm()
+    bpc = BYTES_PER_CELL[args.precision]
+    achieved = bpc * cells / (total_ms / K * 1e-3) / 1e9
+    # end to end: host fields in (dugks_batch_add), the same K steps, every phi back to host
+    t0 = time.perf_counter()
+    outs = [batch.phi(i) for i in ids]
+    t_read = time.perf_counter() - t0
+    e2e_s = t_add + total_ms * 1e-3 + t_read
+    tsize = 8 if args.precision == "fp64" else 4
+    e2e = {"value": cells * K * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(cells * 8 / K), "d2h_bytes_per_step": int(cells * tsize / K),
+           "path": "dugks_batch_add from host fields + K steps + dugks_batch_read_phi of every grid, amortised over K"}
+    batch.close()
+    del outs
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "fp16f": "f32 (f16 storage)"}[args.precision],
+            "data": "synthetic", "config": desc,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "batch_fast_kernel + batch_advance_kernel (graph-replayed)",
+                         "bytes_per_cell": bpc, "peak_source": peak_kind},
+            "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, local):
+    """Continuous-batching server on a seeded Poisson trace (200 requests/s, sides
+    log-uniform 64..2048, 500..20000 steps, rotation or vortex), FP32 order-3
+    upwind, with a resident 4096^2 vortex grid. The trace offers far more work
+    than one GPU does, so it is replayed twice: as recorded (overloaded: the
+    latencies are mostly queueing) and with arrivals stretched so that the
+    offered load is 70% of the throughput measured in the first pass."""
+    import torch
+    from paper_2007_07760_gb300 import native as N
+    from paper_2007_07760_gb300 import server as S
+
+    trace = S.poisson_trace(args.requests, rate=200.0)
+    work = sum(r.cells * r.steps for r in trace)
+    common = dict(W=4.0, M=0.02, cfl=0.8, order=3, flux=0, stages=2, precision="fp32")
+    passes = {}
+    for name, scale in (("recorded", 1.0), ("load70", None)):
+        if scale is None:
+            cap = passes["recorded"]["cell_updates_per_s"]
+            offered = work / trace[-1].arrival
+            scale = min(1.0, 0.7 * cap / offered)
+        stream = torch.cuda.Stream()
+        with N.Batch(stream=stream.cuda_stream, **common) as b:
+            srv = S.Server(b, budget_bytes=int(args.budget_gb * (1 << 30)), slice_steps=64)
+            if not args.no_resident:
+                big = WL.vortex1024(n=4096)
+                srv.add_resident(big.phi0, big.vel_kind, big.vel)
+            with ClockSampler(local) as clk:
+                st = srv.run(trace, time_scale=scale)
+            st["clocks"] = clk.summary()
+            st["time_scale"] = scale
+            passes[name] = st
+    rec = passes["recorded"]
+    line = {"metric": "served D2Q9 cell-updates/s", "value": rec["cell_updates_per_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": sum(r.steps for r in trace), "warmup": 0,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serve{args.requests}_fp32_p3_upwind_2stage", "requests": args.requests,
+                       "rate_per_s": 200.0, "sides": "log-uniform 64..2048", "steps": "log-uniform 500..20000",
+                       "resident_grid": None if args.no_resident else "4096x4096 vortex",
+                       "budget_gb": args.budget_gb, "slice_steps": 64},
+            "serving": passes,
+            "clocks": rec["clocks"], "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,11 +446,19 @@ def main():
     ap.add_argument("--workload", default="slotted_disk256")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16f"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--generic", action="store_true", help="time the generic (plain) kernel instead")
+    ap.add_argument("--requests", type=int, default=48, help="serve workload: requests in the trace")
+    ap.add_argument("--budget-gb", type=float, default=32.0, help="serve workload: device-memory budget")
+    ap.add_argument("--no-resident", action="store_true", help="serve workload: no standing 4096^2 grid")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        run_serve(args, int(os.environ.get("LOCAL_RANK", "0")))
     else:
         run_ours(args)
 

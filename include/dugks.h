@@ -123,6 +123,15 @@ int dugks_status(dugks_ctx *c);
 /* Text of the last error; never NULL (empty when there was none). */
 const char *dugks_last_error(const dugks_ctx *c);
 
+/* Tile variant of the TMA-staged two-stage kernel (orders 2, 3): 0..3 = 8 warps
+ * x 4 rows per thread (FP64: 2), 16 x 1, 8 x 2, 16 x 2; -1 selects the generic
+ * fused kernel (one thread per cell and stage, no TMA), the plain comparison
+ * path. A tuning choice only: results agree to rounding. Ignored for order 4
+ * and the three-stage scheme, which always use the generic kernel.
+ * dugks_get_variant returns -1 when the context uses the generic kernel. */
+int dugks_set_variant(dugks_ctx *c, int variant);
+int dugks_get_variant(const dugks_ctx *c);
+
 /* Number of steps taken since creation (or as restored by dugks_load_state). */
 int64_t dugks_step_index(const dugks_ctx *c);
 

@@ -1,0 +1,82 @@
+"""Autotuner of the fast kernel's tile variant (warps per CTA x rows per thread).
+
+Times each variant on the caller's own solver or batch (CUDA events on its
+stream, after warm-up) and caches the winner per (kind, precision, order, flux,
+size bucket) in a JSON file under the user's cache directory. Results of the
+method do not depend on the variant (the tests check bitwise equality), so the
+choice is purely a speed one. Temporal blocking is not offered: the step kernel
+is bound by instruction issue, not by HBM, so recomputing halos to save HBM
+round trips would slow it down.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+VARIANTS = (0, 1, 2, 3)
+
+
+def _cache_path() -> str:
+    base = os.environ.get("XDG_CACHE_HOME") or os.path.join(os.path.expanduser("~"), ".cache")
+    return os.path.join(base, "dugks_gb300", "tune.json")
+
+
+def _load() -> dict:
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(d: dict):
+    path = _cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
+def key(kind: str, params, cells: int) -> str:
+    bucket = int(round(math.log2(max(cells, 1))))
+    return f"{kind}/p{params.precision}/o{params.order}/f{params.flux}/c2^{bucket}"
+
+
+def _time_steps(step_fn, sync_fn, steps: int) -> float:
+    import torch
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sync_fn()
+    start.record()
+    step_fn(steps)
+    end.record()
+    sync_fn()
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / steps
+
+
+def tune(obj, kind: str, cells: int, steps: int = 20, warmup: int = 3, use_cache: bool = True) -> int:
+    """Pick the fastest variant for `obj` (a native.Solver or native.Batch), set it
+    and return it. The state advances by (warmup + steps) * len(VARIANTS) steps
+    unless the cache answers."""
+    k = key(kind, obj.params, cells)
+    cache = _load() if use_cache else {}
+    if k in cache:
+        obj.set_variant(int(cache[k]["variant"]))
+        return int(cache[k]["variant"])
+    times = {}
+    for v in VARIANTS:
+        obj.set_variant(v)
+        obj.step(warmup)
+        times[v] = _time_steps(obj.step, obj.status, steps)
+    best = min(times, key=times.get)
+    obj.set_variant(best)
+    cache = _load()
+    cache[k] = {"variant": best, "ms_per_step": times, "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    _store(cache)
+    return best

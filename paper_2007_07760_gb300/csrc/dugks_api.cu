@@ -608,6 +608,42 @@ int dugks_status(dugks_ctx *c) {
     return DUGKS_OK;
 }
 
+int dugks_set_variant(dugks_ctx *c, int variant) {
+    if (!c || variant < -1 || variant >= FAST_VARIANTS) return DUGKS_EINVAL;
+    const bool fast_capable = c->p.stages == 2 && c->p.order <= 3 && encode_fn() != nullptr;
+    if (!fast_capable) return DUGKS_OK;   // only the two-stage order-2/3 path has variants
+    cudaSetDevice(c->dev);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    if (variant < 0) {   // the generic kernel (the plain reference GPU step)
+        c->fast = false;
+        c->tile_w = TILE_X;
+        c->tile_h = TILE_Y;
+    } else {
+        c->fast = true;
+        c->variant = variant;
+        const bool ok = c->p.precision == DUGKS_FP64 ? setup_fast<double, double>(c)
+                        : c->p.precision == DUGKS_FP32 ? setup_fast<float, float>(c)
+                                                       : setup_fast<float, __half>(c);
+        if (!ok) return fail(c, DUGKS_ECUDA, "tensor map encoding failed");
+    }
+    c->tiles_x = (c->p.nx + c->tile_w - 1) / c->tile_w;
+    const int ntiles = c->tiles_x * ((c->p.ny + c->tile_h - 1) / c->tile_h);
+    if (ntiles > c->ntiles) {
+        cudaFree(c->partial);
+        c->partial = nullptr;
+        if (cudaMalloc(&c->partial, (size_t)ntiles * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, DUGKS_ENOMEM, "mass partials");
+        }
+    }
+    c->ntiles = ntiles;
+    c->mass_valid = false;
+    return DUGKS_OK;
+}
+
+int dugks_get_variant(const dugks_ctx *c) { return c ? (c->fast ? c->variant : -1) : -1; }
+
 const char *dugks_last_error(const dugks_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 int64_t dugks_step_index(const dugks_ctx *c) { return c ? c->step : -1; }

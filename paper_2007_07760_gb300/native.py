@@ -53,6 +53,8 @@ SIGNATURES = [
     ("dugks_status", ctypes.c_int, [_VP]),
     ("dugks_last_error", ctypes.c_char_p, [_VP]),
     ("dugks_step_index", _I64, [_VP]),
+    ("dugks_set_variant", ctypes.c_int, [_VP, ctypes.c_int]),
+    ("dugks_get_variant", ctypes.c_int, [_VP]),
     ("dugks_state_bytes", ctypes.c_size_t, [_VP]),
     ("dugks_save_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(_I64)]),
     ("dugks_load_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t, _I64]),
@@ -161,6 +163,14 @@ def dugks_last_error(ctx) -> str:
 
 def dugks_step_index(ctx) -> int:
     return lib().dugks_step_index(ctx)
+
+
+def dugks_set_variant(ctx, variant: int):
+    _check(ctx, lib().dugks_set_variant(ctx, int(variant)))
+
+
+def dugks_get_variant(ctx) -> int:
+    return lib().dugks_get_variant(ctx)
 
 
 def dugks_state_bytes(ctx) -> int:
@@ -383,6 +393,9 @@ class Solver:
     @property
     def step_index(self) -> int:
         return dugks_step_index(self.ctx)
+
+    def set_variant(self, v: int):
+        dugks_set_variant(self.ctx, v)
 
     def status(self) -> int:
         return dugks_status(self.ctx)

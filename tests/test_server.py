@@ -1,0 +1,125 @@
+"""Request server: admission, continuous batching and time-to-result.
+
+The policy is tested on the CPU with a stand-in backend whose clock advances
+with the work done; the GPU test checks that every served result equals the
+same request solved alone."""
+import numpy as np
+import pytest
+
+from paper_2007_07760_gb300 import server as S
+
+
+class FakeBatch:
+    """Batch interface without a device: steps cost cells * 1 ns of fake time."""
+
+    def __init__(self, clock):
+        self.clock = clock
+        self.grids = {}
+        self.next = 0
+        self.live_bytes = 0
+        self.max_live_bytes = 0
+
+    def grid_bytes(self, nx, ny):
+        return nx * ny * 80
+
+    def add(self, phi0, kind, vel, target):
+        gid = self.next
+        self.next += 1
+        ny, nx = phi0.shape
+        self.grids[gid] = [0, target, nx * ny]
+        self.live_bytes += nx * ny * 80
+        self.max_live_bytes = max(self.max_live_bytes, self.live_bytes)
+        return gid
+
+    def step(self, n):
+        work = 0
+        for g in self.grids.values():
+            adv = n if g[1] < 0 else max(0, min(n, g[1] - g[0]))
+            g[0] += adv
+            work += adv * g[2]
+        self.clock.t += work * 1e-9
+
+    def step_index(self, gid):
+        return self.grids[gid][0]
+
+    def phi(self, gid):
+        return np.zeros(1)
+
+    def remove(self, gid):
+        self.live_bytes -= self.grids[gid][2] * 80
+        del self.grids[gid]
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-4)
+
+
+def small_trace(count=30, rate=400.0, seed=3):
+    return S.poisson_trace(count, rate=rate, seed=seed, nmin=32, nmax=256, smin=50, smax=400)
+
+
+def test_trace_statistics():
+    tr = S.poisson_trace(4000, rate=200.0, seed=1)
+    gaps = np.diff([0.0] + [r.arrival for r in tr])
+    assert abs(gaps.mean() - 1 / 200.0) < 0.1 / 200.0
+    n = np.array([r.n for r in tr])
+    assert n.min() >= 64 and n.max() <= 2048
+    assert abs(np.median(np.log(n)) - 0.5 * (np.log(64) + np.log(2048))) < 0.1
+    assert 0.45 < np.mean([r.kind == "rotation" for r in tr]) < 0.55
+
+
+def test_policy_budget_fifo_and_overlap():
+    clock = FakeClock()
+    fb = FakeBatch(clock)
+    budget = 3 * 256 * 256 * 80
+    srv = S.Server(fb, budget_bytes=budget, max_slots=8, slice_steps=16, clock=clock, sleep=clock.sleep)
+    trace = small_trace()
+    st = srv.run(trace)
+    assert st["requests"] == len(trace)
+    assert fb.max_live_bytes <= budget and st["peak_bytes"] <= budget
+    res = {r.rid: r for r in srv.results}
+    # first-come first-served admission
+    adm = [res[r.rid].admitted for r in sorted(trace, key=lambda r: r.arrival)]
+    assert all(a <= b + 1e-12 for a, b in zip(adm, adm[1:]))
+    # continuous batching: requests join while others are running
+    overlaps = sum(1 for a in res.values() for b in res.values()
+                   if a.rid != b.rid and a.admitted < b.admitted < a.finished)
+    assert overlaps > 0
+    for r in trace:
+        assert res[r.rid].latency >= 0 and res[r.rid].finished >= r.arrival
+    assert st["p99_s"] >= st["p50_s"] > 0
+
+
+def test_request_larger_than_budget_rejected():
+    clock = FakeClock()
+    srv = S.Server(FakeBatch(clock), budget_bytes=1000, clock=clock, sleep=clock.sleep)
+    with pytest.raises(ValueError):
+        srv.run(small_trace(count=2))
+
+
+@pytest.mark.gpu
+def test_served_results_equal_solo_runs():
+    from paper_2007_07760_gb300 import native as N
+    common = dict(W=4.0, M=0.02, cfl=0.8, order=3, flux=0, stages=2, precision="fp32")
+    trace = S.poisson_trace(14, rate=2000.0, seed=7, nmin=32, nmax=96, smin=20, smax=120)
+    with N.Batch(**common) as b:
+        budget = 3 * b.grid_bytes(96, 96)
+        srv = S.Server(b, budget_bytes=budget, slice_steps=8, keep_fields=True)
+        st = srv.run(trace)
+    assert st["requests"] == len(trace) and st["status"] == 0
+    res = {r.rid: r for r in srv.results}
+    for req in trace:
+        assert np.isfinite(res[req.rid].phi).all()
+        phi0, kind, vel = S.request_field(req)
+        with N.Batch(**common) as solo:
+            g = solo.add(phi0, kind, vel, req.steps)
+            solo.step(req.steps + 5)
+            assert solo.step_index(g) == req.steps
+            assert np.array_equal(solo.phi(g), res[req.rid].phi)
