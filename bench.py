@@ -339,7 +339,7 @@ def run_batch(args, dist, world, rank, local):
                     stream=stream.cuda_stream)
     ids = [batch.add(q.phi0, q.vel_kind, q.vel) for q in probs]
     t_add = time.perf_counter() - t_e2e0
-    variant = autotune.tune(batch, "batch", cells, steps=8, warmup=2)
+    variant = autotune.tune(batch, "batch", cells)
     desc["tile_variant"] = variant
     desc["l2"] = "no flush: the state of all grids is larger than L2"
     batch.step(args.warmup)

@@ -9,7 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libdugks.so")
-SOURCES = ["dugks_api.cu", "dugks_inst_f64.cu", "dugks_inst_f32.cu", "dugks_inst_f16.cu", "dugks_noalloc.cu", "dugks_batch.cu"]
+SOURCES = ["dugks_api.cu", "dugks_noalloc.cu", "dugks_batch.cu"] + [
+    f"dugks_inst_{p}_{k}.cu" for p in ("f64", "f32", "f16") for k in ("gen", "fast", "batch")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
@@ -41,7 +42,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
     r = subprocess.run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)

@@ -15,7 +15,7 @@ import math
 import os
 import time
 
-VARIANTS = (0, 1, 2, 3)
+VARIANTS = (0, 1, 2, 3, 4, 5)
 
 
 def _cache_path() -> str:
@@ -60,10 +60,11 @@ def _time_steps(step_fn, sync_fn, steps: int) -> float:
     return start.elapsed_time(end) / steps
 
 
-def tune(obj, kind: str, cells: int, steps: int = 20, warmup: int = 3, use_cache: bool = True) -> int:
+def tune(obj, kind: str, cells: int, steps: int = 24, warmup: int = 8, use_cache: bool = True) -> int:
     """Pick the fastest variant for `obj` (a native.Solver or native.Batch), set it
     and return it. The state advances by (warmup + steps) * len(VARIANTS) steps
-    unless the cache answers."""
+    unless the cache answers. The warm-up covers one full graph-replay chunk of a
+    batch, so graph capture happens before the timed steps."""
     k = key(kind, obj.params, cells)
     cache = _load() if use_cache else {}
     if k in cache:

@@ -426,16 +426,9 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     // the TMA-staged kernel serves the two-stage scheme at orders 2 and 3
     c->fast = p->stages == 2 && p->order <= 3 && encode_fn() != nullptr;
     if (c->fast) {
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
-        const FastGeom big = p->precision == DUGKS_FP64 ? Launch<double, double>::fast_geom(0)
-                             : p->precision == DUGKS_FP32 ? Launch<float, float>::fast_geom(0)
-                                                          : Launch<float, __half>::fast_geom(0);
-        (void)big;
-        (void)sms;
         // 8 warps x 2 rows per thread measured fastest from 256^2 to 2048^2 (FP32)
         c->variant = 2;
-        // tuning override (set by the autotuner): DUGKS_FAST_VARIANT = 0..3
+        // tuning override: DUGKS_FAST_VARIANT = 0..FAST_VARIANTS-1
         if (const char *ev = std::getenv("DUGKS_FAST_VARIANT")) {
             const int v = std::atoi(ev);
             if (v >= 0 && v < FAST_VARIANTS) c->variant = v;

@@ -42,7 +42,8 @@ struct dugks_batch {
     bool own_stream = false;
     size_t tsize = 4, ssize = 4;
     int nphi = 2;
-    int variant = 2;
+    // 8 warps x 3 rows per thread measured fastest on mixed batches (FP32)
+    int variant = 4;
     int ctas = 0;
     std::vector<Slot> slots;
     // device side
