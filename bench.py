@@ -1,13 +1,19 @@
 """Benchmark of the DUGKS time step on one GB300 (or N replicas under torchrun).
 
-Default workload: the 256 x 256 slotted disk under rigid rotation (FP32,
-order-3 isotropic upwind reconstruction, two-stage DUGKS, M = 0.002, W = 4,
-cfl = 0.8). One benchmark step = one pass of the whole hot path: the fused
-DUGKS step kernel (cell quantities, gradients, face reconstruction, face
-distribution, meso-flux update, per-tile mass partials) plus the global FP64
-mass reduction. The state (2.6 MB) fits in L2, so L2 is flushed (512 MiB write)
-before every timed step and only the step itself is timed, with CUDA events on
-the solver's stream.
+Default workload: single-vortex deformation of a drop on a 1024 x 1024 grid
+(FP32, order-3 isotropic upwind reconstruction, two-stage DUGKS, M = 0.02,
+W = 4, cfl = 0.8, amplitude 0.05, reversal period 8192 steps). One benchmark
+step = one pass of the whole hot path: the fused DUGKS step kernel (cell
+quantities, gradients, face reconstruction, face distribution, meso-flux
+update, per-tile FP64 mass partials) plus the global FP64 mass reduction. The
+state (84 MB) fits in L2, so L2 is flushed (512 MiB write) before every timed
+step and only the step itself is timed, with CUDA events on the solver's stream.
+
+Beside the main line (N = 1 only) the same JSON line carries, under "also", the
+256 x 256 slotted-disk rotation (L2-resident and latency-bound: one partial
+wave of tiles), the 512-grid batch (one graph-replayed launch per step over all
+grids) and the plain single-grid FP64 GPU step (the generic kernel) on the main
+workload, each with its own roofline fraction.
 
 Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead
 (the baseline program for this method) on the same workload.
@@ -182,6 +188,80 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_single(solver, stream, warmup: int, K: int, dist=None, local: int = 0):
+    """W untimed and K timed steps of one solver, L2 flushed before each. One step
+    = the step kernel (per-tile FP64 mass partials) + the kernel that sums them;
+    the second is launched as a programmatic dependent of the first, so no event
+    sits between them in the timed pass. A second pass of K steps, with events
+    around the step kernel alone, gives its duration for the roofline."""
+    import torch
+    from paper_2007_07760_gb300 import native as N
+
+    mass_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush.zero_()
+            N.dugks_step(solver.ctx, 1)
+            N.dugks_mass_device(solver.ctx, mass_dev.data_ptr())
+    stream.synchronize()
+    whole = [(ev(), ev()) for _ in range(K)]
+    kern = [(ev(), ev()) for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            for a, b in whole:
+                flush.zero_()
+                a.record(stream)
+                N.dugks_step(solver.ctx, 1)
+                N.dugks_mass_device(solver.ctx, mass_dev.data_ptr())
+                b.record(stream)
+            for a, b in kern:
+                flush.zero_()
+                a.record(stream)
+                N.dugks_step(solver.ctx, 1)
+                b.record(stream)
+                N.dugks_mass_device(solver.ctx, mass_dev.data_ptr())
+        stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.summary()
+    del flush
+    if N.dugks_status(solver.ctx) != 0:
+        raise SystemExit("device error: " + N.dugks_last_error(solver.ctx))
+    mass = float(mass_dev.item())
+    if not math.isfinite(mass):
+        raise SystemExit("non-finite mass")
+    return {"total_ms": sum(a.elapsed_time(b) for a, b in whole),
+            "avg_step_ms": sum(a.elapsed_time(b) for a, b in kern) / K, "clocks": clocks, "mass": mass}
+
+
+def also_single(name: str, precision: str, K: int, generic: bool = False):
+    """Secondary single-grid measurement for the "also" list of the JSON line."""
+    import torch
+    from paper_2007_07760_gb300 import native as N
+
+    prob, desc = workload(name, precision)
+    stream = torch.cuda.Stream()
+    with N.Solver.from_problem(prob, precision=precision, stream=stream.cuda_stream) as solver:
+        if generic:
+            solver.set_variant(-1)
+        r = time_single(solver, stream, 10, K)
+    peak, _ = measured_peak_hbm()
+    achieved = BYTES_PER_CELL[precision] * prob.cells / (r["avg_step_ms"] * 1e-3) / 1e9
+    return {"workload": desc["workload"] + ("_generic_kernel" if generic else ""),
+            "value": prob.cells * K / (r["total_ms"] * 1e-3), "unit": UNIT, "steps": K,
+            "ms_per_step": r["total_ms"] / K,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "avg_kernel_ms": r["avg_step_ms"]},
+            "clocks": r["clocks"]}
+
+
 def run_ours(args):
     import torch
     from paper_2007_07760_gb300 import native as N
@@ -209,52 +289,16 @@ def run_ours(args):
     if args.generic:
         solver.set_variant(-1)
         desc["kernel"] = "generic step_kernel (plain comparison path)"
-    mass_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    def one_step():
-        N.dugks_step(solver.ctx, 1)
-        N.dugks_mass_device(solver.ctx, mass_dev.data_ptr())
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.zero_()
-            one_step()
-    stream.synchronize()
-
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            for i in range(K):
-                flush.zero_()
-                ev[i][0].record(stream)
-                N.dugks_step(solver.ctx, 1)
-                ev[i][1].record(stream)
-                N.dugks_mass_device(solver.ctx, mass_dev.data_ptr())
-                ev[i][2].record(stream)
-        stream.synchronize()
-    torch.cuda.synchronize()
-    clocks = clk.summary()
-    step_ms = [a.elapsed_time(b) for a, b, _ in ev]
-    total_ms = sum(a.elapsed_time(c) for a, _, c in ev)
+    res = time_single(solver, stream, args.warmup, K, dist, local)
+    total_ms, avg_step_ms, clocks, mass = res["total_ms"], res["avg_step_ms"], res["clocks"], res["mass"]
     if dist:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    if N.dugks_status(solver.ctx) != 0:
-        raise SystemExit("device error: " + N.dugks_last_error(solver.ctx))
-    mass = float(mass_dev.item())
-    if not math.isfinite(mass):
-        raise SystemExit("non-finite mass")
 
     value = prob.cells * K * world / (total_ms * 1e-3)
-    avg_step_ms = sum(step_ms) / K
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_CELL[args.precision] * prob.cells / (avg_step_ms * 1e-3) / 1e9
     sha = kernel_source_hash()
@@ -297,6 +341,7 @@ def run_ours(args):
             "dtype": {"fp64": "f64", "fp32": "f32", "fp16f": "f32 (f16 storage)"}[args.precision],
             "data": "synthetic",
             "config": dict(desc, l2="flushed before every timed step (512 MiB write, untimed)",
+                           mass="FP64 per-tile partials in the step kernel + fixed-order sum kernel",
                            replicas=world, parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -310,41 +355,43 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if world == 1 and not args.no_also:
+            line["also"] = [also_single("slotted_disk256", "fp32", 300), also_batch(512, "fp32", 64),
+                            also_single(args.workload, "fp64", 20, generic=True)]
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batch(args, dist, world, rank, local):
-    """Many independent grids (512, sides log-uniform 64..512, 1-8 drops, uniform
-    velocity |u| <= 0.05) advanced together: one launch per step over a work
-    list of tiles of all grids, replayed as CUDA graphs. The state (2.3 GB in
-    FP32) is far larger than L2, so no flush is needed between steps."""
+def measure_batch(count: int, precision: str, warmup: int, K: int, dist=None, local: int = 0):
+    """Many independent grids (sides log-uniform 64..512, 1-8 drops, uniform velocity
+    |u| <= 0.05) advanced together: one launch per step over a work list of tiles
+    of all grids, replayed as CUDA graphs, tile variant picked by the autotuner.
+    The state of 512 grids (2.3 GB in FP32) is far larger than L2, so no flush is
+    needed between steps."""
     import torch
     from paper_2007_07760_gb300 import autotune
     from paper_2007_07760_gb300 import native as N
 
-    count = int(args.workload[len("batch"):] or 512)
     probs = WL.random_batch(count=count)
     p0 = probs[0]
     stream = torch.cuda.Stream()
-    desc = {"workload": f"batch{count}_{args.precision}_p{p0.order}_upwind_2stage", "grids": count,
-            "sides": "log-uniform 64..512 (seeded)", "precision": args.precision, "order": p0.order,
+    desc = {"workload": f"batch{count}_{precision}_p{p0.order}_upwind_2stage", "grids": count,
+            "sides": "log-uniform 64..512 (seeded)", "precision": precision, "order": p0.order,
             "flux": "upwind", "stages": 2, "M": p0.M, "cfl": p0.cfl, "W": p0.W,
             "velocity": "uniform, random angle, |u| <= 0.05"}
     cells = sum(q.cells for q in probs)
     desc["cells"] = cells
     t_e2e0 = time.perf_counter()
-    batch = N.Batch(precision=args.precision, W=p0.W, M=p0.M, cfl=p0.cfl, order=p0.order, flux=0, stages=2,
+    batch = N.Batch(precision=precision, W=p0.W, M=p0.M, cfl=p0.cfl, order=p0.order, flux=0, stages=2,
                     stream=stream.cuda_stream)
     ids = [batch.add(q.phi0, q.vel_kind, q.vel) for q in probs]
     t_add = time.perf_counter() - t_e2e0
     variant = autotune.tune(batch, "batch", cells)
     desc["tile_variant"] = variant
     desc["l2"] = "no flush: the state of all grids is larger than L2"
-    batch.step(args.warmup)
+    batch.step(warmup)
     batch.status()
-    K = args.steps
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
@@ -359,6 +406,23 @@ def run_batch(args, dist, world, rank, local):
     total_ms = ev0.elapsed_time(ev1)
     if batch.status() != 0:
         raise SystemExit("device error: " + N.dugks_batch_last_error(batch.b))
+    # end to end: host fields in (dugks_batch_add), the same K steps, every phi back to host
+    t0 = time.perf_counter()
+    outs = [batch.phi(i) for i in ids]
+    t_read = time.perf_counter() - t0
+    batch.close()
+    del outs
+    return {"desc": desc, "cells": cells, "total_ms": total_ms, "clocks": clocks,
+            "e2e_s": t_add + total_ms * 1e-3 + t_read}
+
+
+def run_batch(args, dist, world, rank, local):
+    import torch
+
+    count = int(args.workload[len("batch"):] or 512)
+    K = args.steps
+    r = measure_batch(count, args.precision, args.warmup, K, dist, local)
+    total_ms, cells, desc = r["total_ms"], r["cells"], r["desc"]
     if dist:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -367,17 +431,10 @@ def run_batch(args, dist, world, rank, local):
     peak, peak_kind = measured_peak_hbm()
     bpc = BYTES_PER_CELL[args.precision]
     achieved = bpc * cells / (total_ms / K * 1e-3) / 1e9
-    # end to end: host fields in (dugks_batch_add), the same K steps, every phi back to host
-    t0 = time.perf_counter()
-    outs = [batch.phi(i) for i in ids]
-    t_read = time.perf_counter() - t0
-    e2e_s = t_add + total_ms * 1e-3 + t_read
     tsize = 8 if args.precision == "fp64" else 4
-    e2e = {"value": cells * K * world / e2e_s, "unit": UNIT,
+    e2e = {"value": cells * K * world / r["e2e_s"], "unit": UNIT,
            "h2d_bytes_per_step": int(cells * 8 / K), "d2h_bytes_per_step": int(cells * tsize / K),
            "path": "dugks_batch_add from host fields + K steps + dugks_batch_read_phi of every grid, amortised over K"}
-    batch.close()
-    del outs
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -387,9 +444,20 @@ def run_batch(args, dist, world, rank, local):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "batch_fast_kernel + batch_advance_kernel (graph-replayed)",
                          "bytes_per_cell": bpc, "peak_source": peak_kind},
-            "e2e": e2e, "gpu_launches": 2 * K, "clocks": clocks,
+            "e2e": e2e, "gpu_launches": 2 * K, "clocks": r["clocks"],
         }
         print(json.dumps(line), flush=True)
+
+
+def also_batch(count: int, precision: str, K: int):
+    r = measure_batch(count, precision, 8, K)
+    peak, _ = measured_peak_hbm()
+    achieved = BYTES_PER_CELL[precision] * r["cells"] / (r["total_ms"] / K * 1e-3) / 1e9
+    return {"workload": r["desc"]["workload"], "value": r["cells"] * K / (r["total_ms"] * 1e-3), "unit": UNIT,
+            "steps": K, "ms_per_step": r["total_ms"] / K, "cells": r["cells"],
+            "tile_variant": r["desc"]["tile_variant"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak},
+            "clocks": r["clocks"]}
 
 
 def run_serve(args, local):
@@ -440,12 +508,13 @@ def run_serve(args, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="slotted_disk256")
+    ap.add_argument("--workload", default="vortex1024")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16f"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-also", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--generic", action="store_true", help="time the generic (plain) kernel instead")
     ap.add_argument("--requests", type=int, default=48, help="serve workload: requests in the trace")
     ap.add_argument("--budget-gb", type=float, default=32.0, help="serve workload: device-memory budget")

@@ -2,9 +2,9 @@
 
 Times each variant on the caller's own solver or batch (CUDA events on its
 stream, after warm-up) and caches the winner per (kind, precision, order, flux,
-size bucket) in a JSON file under the user's cache directory. Results of the
-method do not depend on the variant (the tests check bitwise equality), so the
-choice is purely a speed one. Temporal blocking is not offered: the step kernel
+size bucket) in a JSON file under the user's cache directory. The variants
+run the same per-cell arithmetic (they agree to rounding; the tests check it
+against the oracle and against each other), so the choice is a speed one. Temporal blocking is not offered: the step kernel
 is bound by instruction issue, not by HBM, so recomputing halos to save HBM
 round trips would slow it down.
 """

@@ -374,6 +374,8 @@ namespace dugks {
 // Fixed-order sum of the per-tile partials (deterministic); flags NaN / Inf.
 __global__ void __launch_bounds__(256) mass_final_kernel(const double *partial, int n, double *out, int *status) {
     __shared__ double sred[32];
+    pdl_trigger();
+    pdl_wait();   // the partials of the step kernel ahead of it
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
     s = block_sum(s, sred);
@@ -384,7 +386,19 @@ __global__ void __launch_bounds__(256) mass_final_kernel(const double *partial, 
 }
 
 cudaError_t launch_mass_final(const double *partial, int n, double *out, int *status, cudaStream_t s) {
-    mass_final_kernel<<<1, 256, 0, s>>>(partial, n, out, status);
+    // programmatic dependent launch: resident while the step kernel drains, it
+    // waits for the partials in the kernel itself
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, mass_final_kernel, partial, n, out, status);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 }  // namespace dugks

@@ -589,8 +589,13 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = fast_bar<T, ST, NW, MR>(smem);
     if (threadIdx.x == 0) mbar_init(bar, 1);
+    pdl_wait();   // the previous kernel's output (launched with programmatic serialization)
     double *mo = p.mass_partial ? p.mass_partial + blockIdx.y * p.tiles_x + blockIdx.x : nullptr;
     fast_tile<T, ST, ORDER, FLUX, NW, MR>(p, cf, fe_, &tmX, &tmPo, &tmPc, blockIdx.x, blockIdx.y, mo, smem, bar, 0);
+    // the next kernel may be scheduled once every tile is done with its work (a
+    // trigger at entry would place its waiting CTAs while this grid still runs,
+    // unevenly when the grid is a single wave)
+    pdl_trigger();
 }
 
 // ---- many grids per launch ----------------------------------------------------

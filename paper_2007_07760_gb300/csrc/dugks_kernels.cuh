@@ -116,6 +116,15 @@ __device__ __forceinline__ void put_cell(const StepParams<T> &p, V *plane, int x
     }
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with programmatic
+// stream serialization may be scheduled before the kernel ahead of it in the
+// stream has finished, once every CTA of that kernel has signalled (pdl_trigger)
+// or exited; it must then wait (pdl_wait) for that kernel to complete, with its
+// memory visible, before reading its results. Both are no-ops for a kernel
+// launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ int wrapc(int i, int n) {
     i %= n;
     return i < 0 ? i + n : i;

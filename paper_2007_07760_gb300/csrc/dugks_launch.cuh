@@ -104,9 +104,18 @@ static cudaError_t launch_fast_t(const StepParams<T> &p, const FaceCoefs<T> &cf,
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    dim3 grid((p.nx + FT::TX - 1) / FT::TX, (p.ny + FT::TY - 1) / FT::TY);
-    kern<<<grid, FT::NT, FT::smem_bytes, s>>>(p, cf, fe, tmX, tmPo, tmPc);
-    return cudaGetLastError();
+    // programmatic dependent launch: scheduled while the previous kernel drains
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nx + FT::TX - 1) / FT::TX, (p.ny + FT::TY - 1) / FT::TY);
+    cfg.blockDim = dim3(FT::NT);
+    cfg.dynamicSmemBytes = FT::smem_bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p, cf, fe, tmX, tmPo, tmPc);
 }
 
 template <typename T, typename ST, int ORDER, int FLUX>

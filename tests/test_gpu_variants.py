@@ -1,0 +1,118 @@
+"""Tile variants of the TMA-staged two-stage kernel (warps x rows per thread).
+
+Every variant of each precision against the FP64 oracle on a ragged grid that
+spans several tiles in both directions with a partial last tile, all velocity
+kinds; the FP32 variants against each other (same per-cell arithmetic; the
+compiler may contract it differently per instantiation, so they agree to
+rounding); the batch path with every variant against the single-grid path;
+and the rejection of variant numbers outside the table.
+"""
+import numpy as np
+import pytest
+
+from paper_2007_07760_gb300 import native as N
+from paper_2007_07760_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = list(range(6))
+FP32_TOL = 5e-5
+
+
+def problem(nx, ny, kind, seed):
+    rng = np.random.default_rng(WL.SEED_BASE + 40 + seed)
+    cents = [tuple(rng.uniform(0, [nx, ny])) for _ in range(3)]
+    phi0 = WL.drops(nx, ny, cents, [min(nx, ny) / 5, min(nx, ny) / 7, min(nx, ny) / 9], 4.0)
+    vel = {"uniform": (0.03, -0.02), "rotation": (nx / 2, ny / 2, 1.5e-3), "vortex": (float(nx), 0.04, 30.0)}[kind]
+    return phi0, vel
+
+
+def oracle_phi(O, nx, ny, phi0, order, flux, kind, vel, steps):
+    p = O.Params(nx, ny, W=4.0, M=0.02, cfl=0.8, order=order, flux=flux, stages=2, vel_kind=kind, vel=vel)
+    return O.State(p, phi0).run(steps).phi()
+
+
+def solver_phi(nx, ny, phi0, order, flux, kind, vel, steps, precision, variant):
+    with N.Solver(nx, ny, phi0, vel_kind=kind, vel=vel, W=4.0, M=0.02, cfl=0.8, order=order, flux=flux,
+                  stages=2, precision=precision) as s:
+        s.set_variant(variant)
+        assert N.dugks_get_variant(s.ctx) == variant
+        s.step(steps)
+        assert s.status() == 0
+        return s.phi()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("order,flux", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_fp32_variants_match_oracle(oracle, variant, order, flux):
+    nx, ny = 77, 70      # 3 x 5 tiles of 31 x 15, 3 x 3 of 31 x 31: ragged in both directions
+    kind = ["uniform", "rotation", "vortex"][(order + flux + variant) % 3]
+    phi0, vel = problem(nx, ny, kind, seed=order * 2 + flux)
+    ref = oracle_phi(oracle, nx, ny, phi0, order, flux, kind, vel, 60)
+    phi = solver_phi(nx, ny, phi0, order, flux, kind, vel, 60, "fp32", variant)
+    assert np.abs(phi - ref).max() < FP32_TOL
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_fp64_variants_match_oracle(oracle, variant):
+    nx, ny = 77, 70
+    kind = ["uniform", "rotation", "vortex"][variant % 3]
+    phi0, vel = problem(nx, ny, kind, seed=variant)
+    ref = oracle_phi(oracle, nx, ny, phi0, 3, 0, kind, vel, 40)
+    phi = solver_phi(nx, ny, phi0, 3, 0, kind, vel, 40, "fp64", variant)
+    assert np.abs(phi - ref).max() / np.abs(ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_fp16f_variants_error_bounded(oracle, variant):
+    nx, ny = 77, 70
+    phi0, vel = problem(nx, ny, "rotation", seed=11)
+    ref = oracle_phi(oracle, nx, ny, phi0, 3, 0, "rotation", vel, 100)
+    phi = solver_phi(nx, ny, phi0, 3, 0, "rotation", vel, 100, "fp16f", variant)
+    assert np.abs(phi - ref).max() < 2e-3
+
+
+def test_fp32_variants_agree_to_rounding():
+    """Same per-cell arithmetic in every tile shape, up to the contraction of
+    multiply-adds chosen per instantiation."""
+    nx, ny = 96, 64
+    phi0, vel = problem(nx, ny, "vortex", seed=21)
+    ref = solver_phi(nx, ny, phi0, 3, 0, "vortex", vel, 100, "fp32", 2)
+    for v in VARIANTS:
+        assert np.abs(solver_phi(nx, ny, phi0, 3, 0, "vortex", vel, 100, "fp32", v) - ref).max() < 2e-6, v
+
+
+def test_invalid_variants_rejected():
+    phi0, vel = problem(40, 30, "uniform", seed=1)
+    with N.Solver(40, 30, phi0, vel=vel, order=3, precision="fp32") as s:
+        for v in (6, 9, -2):
+            with pytest.raises(N.DugksError):
+                s.set_variant(v)
+        assert N.dugks_get_variant(s.ctx) == 2
+    with N.Batch(precision="fp32", W=4.0, M=0.02, cfl=0.8, order=3, flux=0, stages=2) as b:
+        b.add(phi0, "uniform", vel)
+        for v in (-1, 6):
+            with pytest.raises(N.DugksError):
+                b.set_variant(v)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16f"])
+def test_batch_variants_match_single_grid(precision):
+    """Mixed batch with each variant: every grid equals its single-grid run with the
+    same variant (same tile body; only the host- versus device-computed time
+    factors of the vortex may round differently)."""
+    grids = []
+    for i, (nx, ny, kind) in enumerate([(45, 27, "uniform"), (64, 64, "rotation"), (33, 40, "vortex")]):
+        phi0, vel = problem(nx, ny, kind, seed=30 + i)
+        grids.append((phi0, kind, vel))
+    for v in VARIANTS:
+        with N.Batch(precision=precision, W=4.0, M=0.02, cfl=0.8, order=3, flux=0, stages=2) as b:
+            b.set_variant(v)
+            ids = [b.add(p0, k, vel) for p0, k, vel in grids]
+            b.step(13)
+            assert b.status() == 0
+            for gid, (p0, k, vel) in zip(ids, grids):
+                ny, nx = p0.shape
+                solo = solver_phi(nx, ny, p0, 3, 0, k, vel, 13, precision, v)
+                tol = 2e-6 if precision == "fp32" else 2e-5
+                assert np.abs(b.phi(gid) - solo).max() < tol, (v, gid)
