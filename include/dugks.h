@@ -123,11 +123,14 @@ int dugks_status(dugks_ctx *c);
 /* Text of the last error; never NULL (empty when there was none). */
 const char *dugks_last_error(const dugks_ctx *c);
 
-/* Tile variant of the TMA-staged two-stage kernel (orders 2, 3): 0..3 = 8 warps
- * x 4 rows per thread (FP64: 2), 16 x 1, 8 x 2, 16 x 2; -1 selects the generic
- * fused kernel (one thread per cell and stage, no TMA), the plain comparison
- * path. A tuning choice only: results agree to rounding. Ignored for order 4
- * and the three-stage scheme, which always use the generic kernel.
+/* Tile variant of the TMA-staged two-stage kernel (orders 2, 3), warps per CTA x
+ * rows of cells per thread: 0 = 8 x 4 (FP64: 8 x 2), 1 = 16 x 1, 2 = 8 x 2,
+ * 3 = 16 x 2, 4 = 8 x 3, 5 = 4 x 4 (a tile is 31 cells wide and warps x rows - 1
+ * cells high). The default is 2 below 512 x 512 cells and 4 from there up; -1
+ * selects the generic fused kernel (one thread per cell and stage, no TMA), the
+ * plain comparison path. A tuning choice only: results agree to rounding.
+ * Returns DUGKS_EINVAL for any other number. Ignored for order 4 and the
+ * three-stage scheme, which always use the generic kernel.
  * dugks_get_variant returns -1 when the context uses the generic kernel. */
 int dugks_set_variant(dugks_ctx *c, int variant);
 int dugks_get_variant(const dugks_ctx *c);
@@ -187,7 +190,8 @@ int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host);
 /* Waits and returns one grid's mass (FP64, fixed-order sum). */
 int dugks_batch_mass(dugks_batch *b, int32_t grid_id, double *out);
 
-/* Tile variant of the kernel (0..3; see the design notes); rebuilds descriptors. */
+/* Tile variant of the batch kernel (0..5 as for dugks_set_variant; default 4);
+ * waits for the stream and rebuilds the grid descriptors. */
 int dugks_batch_set_variant(dugks_batch *b, int variant);
 
 /* Cells of all grids that are still advancing. */

@@ -440,8 +440,9 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     // the TMA-staged kernel serves the two-stage scheme at orders 2 and 3
     c->fast = p->stages == 2 && p->order <= 3 && encode_fn() != nullptr;
     if (c->fast) {
-        // 8 warps x 2 rows per thread measured fastest from 256^2 to 2048^2 (FP32)
-        c->variant = 2;
+        // measured (FP32, L2 flushed between steps): 8 warps x 2 rows per thread fastest
+        // on grids that fill about one wave of tiles (256^2), 8 x 3 from 1024^2 up
+        c->variant = (int64_t)p->nx * p->ny >= 512 * 512 ? 4 : 2;
         // tuning override: DUGKS_FAST_VARIANT = 0..FAST_VARIANTS-1
         if (const char *ev = std::getenv("DUGKS_FAST_VARIANT")) {
             const int v = std::atoi(ev);

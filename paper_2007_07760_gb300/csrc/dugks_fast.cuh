@@ -100,6 +100,11 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 
 constexpr uint32_t MBAR_MAX_POLLS = 1u << 22;
 
+// 1 / sqrt(g): correctly rounded in FP64; the hardware reciprocal square root in
+// FP32 (a few ulp, far inside the FP32 tolerance, and no division slow path)
+__device__ __forceinline__ double rnorm(double g) { return 1.0 / sqrt(g); }
+__device__ __forceinline__ float rnorm(float g) { return rsqrtf(g); }
+
 // wrap a tile-relative index into [0, n) (at most a few periods away)
 __device__ __forceinline__ int wrap_small(int i, int n) {
     while (i < 0) i += n;
@@ -194,6 +199,13 @@ struct FastTile {
     static constexpr size_t smem_bytes = oBar + 16;
     static constexpr uint32_t tx_bytes =
         (uint32_t)(sizeof(ST) * 9 * BW * RH + sizeof(T) * BWT * RH * (DEV ? 2 : 1));
+    // resident CTAs per SM that shared memory allows (228 KiB per SM, 1 KiB reserved
+    // per CTA) and threads allow, without asking for fewer than 64 registers per thread:
+    // the register target of the launch bounds, so that registers never cut occupancy
+    // below what shared memory gives
+    static constexpr int cmin(int a, int b) { return a < b ? a : b; }
+    static constexpr int min_blocks =
+        cmin(cmin((int)((228u * 1024u) / (smem_bytes + 1024u)), 2048 / NT), 65536 / (NT * 64));
 };
 
 // One tile (bx, by) of one grid. The caller initialised the mbarrier `bar`
@@ -308,7 +320,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         const T g2 = gxp * gxp + gyp * gyp;
         T nxv = T(0), nyv = T(0);
         if (g2 > T(1e-24)) {  // Eq. (2); n = 0 where grad phi vanishes
-            const T inv = T(1) / sqrt(g2);
+            const T inv = rnorm(g2);
             nxv = gxp * inv;
             nyv = gyp * inv;
         }
@@ -354,8 +366,15 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     // store identical values (no divergent branch in the direction loop)
     int exj[NXS], exX[NXS];
     T eg[NXS], ePx[NXS], ePy[NXS];
+    // a warp whose first slot lies beyond the halo has nothing to do there (warp-uniform)
+    bool exw[NXS];
+#pragma unroll
+    for (int s = 0; s < NXS; s++) exw[s] = warp * 32 + s * NT < NE;
 #pragma unroll
     for (int s = 0; s < NXS; s++) {
+        exj[s] = exX[s] = 0;
+        eg[s] = ePx[s] = ePy[s] = T(0);
+        if (!exw[s]) continue;
         const int e = min(tid + s * NT, NE - 1);
         int x, y;
         if (e < 3 * CH) {
@@ -406,17 +425,19 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             return v;
         };
         // S3a: bar f^+_k = X_k + b (g_k - X_k) (increment form; a + b = 1)
-        T xk[MR], gk[MR];
+        T xk[MR], gk[MR], fo[MR];
 #pragma unroll
         for (int r = 0; r < MR; r++) {
             const ST v = sX[k * RH * BW + xbase + r * BW];
             if constexpr (DEV) xk[r] = wk * (cg[r] + to_f(v) * p.qinv);
             else xk[r] = (T)v;
             gk[r] = wk * (cg[r] + xiP(cPx[r], cPy[r]));
-            F[fbase + r * CW] = xk[r] + p.b * (gk[r] - xk[r]);
+            fo[r] = xk[r] + p.b * (gk[r] - xk[r]);
+            F[fbase + r * CW] = fo[r];
         }
 #pragma unroll
         for (int s = 0; s < NXS; s++) {
+            if (!exw[s]) continue;
             const ST v = sX[k * RH * BW + exX[s]];
             T xe;
             if constexpr (DEV) xe = wk * (eg[s] + to_f(v) * p.qinv);
@@ -434,11 +455,13 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         }
         // S3b: face values of my MR cells from a (MR + 3) x 4 window of bar f^+_k
         // (entries no tap uses are never loaded)
+        // (my own column of rows 0 .. MR - 1 is in registers)
         T win[MR + 3][4];
 #pragma unroll
         for (int i = 0; i < MR + 3; i++)
 #pragma unroll
-            for (int a = 0; a < 4; a++) win[i][a] = F[fbase + (i - 1) * CW + (a - 1)];
+            for (int a = 0; a < 4; a++)
+                win[i][a] = (a == 1 && i >= 1 && i <= MR) ? fo[i - 1] : F[fbase + (i - 1) * CW + (a - 1)];
         T fe[MR], fn[MR];
 #pragma unroll
         for (int r = 0; r < MR; r++) {
@@ -582,7 +605,7 @@ __device__ __forceinline__ uint64_t *fast_bar(unsigned char *smem) {
 
 // One grid, one tile per CTA.
 template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
-__global__ void __launch_bounds__(NW * 32)
+__global__ void __launch_bounds__(NW * 32, (FastTile<T, ST, NW, MR>::min_blocks))
 step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant__ FaceCoefs<T> cf,
                  const __grid_constant__ FastExtra<T> fe_, const __grid_constant__ CUtensorMap tmX,
                  const __grid_constant__ CUtensorMap tmPo, const __grid_constant__ CUtensorMap tmPc) {
@@ -628,7 +651,7 @@ struct BatchUniform {
 };
 
 template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
-__global__ void __launch_bounds__(NW * 32)
+__global__ void __launch_bounds__(NW * 32, (FastTile<T, ST, NW, MR>::min_blocks))
 batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_constant__ FaceCoefs<T> cf,
                   const BatchGrid<T> *__restrict__ grids, const int4 *__restrict__ items, int nitems,
                   double *__restrict__ partials) {
