@@ -43,9 +43,14 @@ UNIT = "cell-updates/s"
 BYTES_PER_CELL = {"fp64": 160, "fp32": 80, "fp16f": 48}   # two-stage, with d(phi u)/dt
 L2_FLUSH_BYTES = 512 << 20
 
-# DRAM traffic of the step kernel from one ncu capture, keyed by the hash of the
-# kernel sources it was taken on (reported as null once the sources change).
-NCU_TRAFFIC = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes) of one step
+# kernel launch from one ncu capture, keyed by the hash of the kernel sources it
+# was taken on and the workload (reported as null once the sources change). The
+# writes of a 1024^2 step stay in L2 (129 MB) during the launch and reach DRAM
+# later, so the figure is the read traffic plus the evictions.
+NCU_TRAFFIC = {
+    ("27f747024f4708d4", "vortex1024_fp32_p3_upwind_2stage"): 45994240,
+}
 
 
 def kernel_source_hash() -> str:
@@ -289,6 +294,9 @@ def run_ours(args):
     if args.generic:
         solver.set_variant(-1)
         desc["kernel"] = "generic step_kernel (plain comparison path)"
+    elif args.variant is not None:
+        solver.set_variant(args.variant)
+        desc["tile_variant"] = args.variant
     elif prob.stages == 2 and prob.order <= 3:
         from paper_2007_07760_gb300 import autotune
         desc["tile_variant"] = autotune.tune(solver, "single", prob.cells)
@@ -522,6 +530,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp16f"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-also", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--variant", type=int, default=None, help="fixed tile variant (default: autotuned)")
     ap.add_argument("--generic", action="store_true", help="time the generic (plain) kernel instead")
     ap.add_argument("--requests", type=int, default=48, help="serve workload: requests in the trace")
     ap.add_argument("--budget-gb", type=float, default=32.0, help="serve workload: device-memory budget")
