@@ -66,9 +66,14 @@ def workload(name: str, precision: str):
     if name == "slotted_disk256":
         prob = WL.slotted_disk256(order=3, flux=0, stages=2)
     elif name.startswith("vortex"):
-        n = int(name[len("vortex"):] or 1024)
-        prob = WL.vortex1024(order=3, flux=0, stages=2, n=n)
-        prob.name = name
+        # vortex<n>[_p<order>][_central][_t3]: the three-stage scheme at cfl 0.5 (it needs dt < 12 tau)
+        parts = name.split("_")
+        n = int(parts[0][len("vortex"):] or 1024)
+        order = next((int(q[1:]) for q in parts[1:] if q.startswith("p")), 3)
+        flux = 1 if "central" in parts[1:] else 0
+        stages = 3 if "t3" in parts[1:] else 2
+        prob = WL.vortex1024(order=order, flux=flux, stages=stages, cfl=0.5 if stages == 3 else 0.8, n=n)
+        prob.name = parts[0]
     elif name == "drop64":
         prob = WL.drop64()
     else:
@@ -258,8 +263,10 @@ def also_single(name: str, precision: str, K: int, generic: bool = False):
             solver.set_variant(-1)
         r = time_single(solver, stream, 10, K)
     peak, _ = measured_peak_hbm()
-    achieved = BYTES_PER_CELL[precision] * prob.cells / (r["avg_step_ms"] * 1e-3) / 1e9
-    return {"workload": desc["workload"] + ("_generic_kernel" if generic else ""),
+    # the three-stage scheme runs two kernels per step, which move 56 values per cell between them
+    bpc = BYTES_PER_CELL[precision] if prob.stages == 2 else {"fp64": 448, "fp32": 224}[precision]
+    achieved = bpc * prob.cells / (r["avg_step_ms"] * 1e-3) / 1e9
+    return {"workload": desc["workload"] + ("_generic_kernel" if generic else ""), "bytes_per_cell": bpc,
             "value": prob.cells * K / (r["total_ms"] * 1e-3), "unit": UNIT, "steps": K,
             "ms_per_step": r["total_ms"] / K,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -372,7 +379,8 @@ def run_ours(args):
             line["cpu_baseline"] = cpu
         if world == 1 and not args.no_also:
             line["also"] = [also_single("slotted_disk256", "fp32", 300), also_batch(512, "fp32", 64),
-                            also_single(args.workload, "fp64", 20, generic=True)]
+                            also_single(args.workload, "fp64", 20, generic=True),
+                            also_single("vortex1024_t3", "fp32", 50), also_single("vortex1024_p4", "fp32", 50)]
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

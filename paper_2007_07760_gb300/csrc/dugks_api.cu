@@ -48,6 +48,8 @@ struct dugks_ctx {
     CUtensorMap tmX[2], tmPhi[3];
     double coef_h = -1.0;
     std::vector<unsigned char> coefs;   // FaceCoefs<T> of the current h
+    double coef3_dt = -1.0;             // three-stage: FaceCoefs<T> at dt / 6 and 5 dt / 12
+    std::vector<unsigned char> coefs3[2];
     int vel_kind = DUGKS_VEL_UNIFORM;
     double vel[4] = {0, 0, 0, 0};
     bool initialized = false;
@@ -237,6 +239,20 @@ int step_t2(dugks_ctx *c) {
     return DUGKS_OK;
 }
 
+// Single-vortex reversal factors cos(pi t / T) at the cell time, the older time
+// of d(phi u)/dt and the face time (FP64 on the host); zero for other velocities.
+template <typename T>
+FastExtra<T> vortex_factors(const dugks_ctx *c, double t, double t_old, double t_face) {
+    FastExtra<T> fx{};
+    if (c->vel_kind == DUGKS_VEL_VORTEX) {
+        const double PI = 3.14159265358979323846, Tp = c->vel[2];
+        fx.vc_t = (T)std::cos(PI * t / Tp);
+        fx.vc_told = (T)std::cos(PI * t_old / Tp);
+        fx.vc_tface = (T)std::cos(PI * t_face / Tp);
+    }
+    return fx;
+}
+
 // One three-stage step (Sec. II.B.2): X[0] = hat f, X[1] = tilde f at t',
 // X[2] = accumulator f^n + (3 dt / 7) L*.
 template <typename T>
@@ -265,7 +281,21 @@ int step_t3(dugks_ctx *c) {
     A.out2 = static_cast<T *>(c->X[2]);
     A.phi_old = static_cast<const T *>(c->phi[c->pr[0]]);
     A.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
-    cudaError_t e = Launch<T, T>::step(A, c->p.order, c->p.flux, KIND_T3A, c->stream);
+    cudaError_t e;
+    if (c->fast && c->coef3_dt != dt) {
+        const FaceCoefs<T> ca = make_face_coefs<T>(c->p.order, c->p.flux, dt / 6.0);
+        const FaceCoefs<T> cb = make_face_coefs<T>(c->p.order, c->p.flux, 5.0 * dt / 12.0);
+        c->coefs3[0].assign(reinterpret_cast<const unsigned char *>(&ca), reinterpret_cast<const unsigned char *>(&ca) + sizeof ca);
+        c->coefs3[1].assign(reinterpret_cast<const unsigned char *>(&cb), reinterpret_cast<const unsigned char *>(&cb) + sizeof cb);
+        c->coef3_dt = dt;
+    }
+    if (c->fast) {
+        const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs3[0].data());
+        e = Launch<T, T>::step_fast3(A, cf, vortex_factors<T>(c, t, t - dt, t + dt / 6.0), c->tmX[0],
+                                     c->tmPhi[c->pr[0]], c->p.order, c->p.flux, KIND_T3A, c->stream);
+    } else {
+        e = Launch<T, T>::step(A, c->p.order, c->p.flux, KIND_T3A, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "three-stage kernel A");
     // (iii)-(iv): bar f^{+, 5dt/12}(t') (Eq. (34)), flux at t_n + 3dt/4, hat f^{n+1}
     StepParams<T> B = base_params<T>(c);
@@ -287,7 +317,13 @@ int step_t3(dugks_ctx *c) {
     B.out1 = c->X[0];
     B.phi_old = static_cast<const T *>(c->phi[c->pr[1]]);
     B.mass_partial = c->partial;
-    e = Launch<T, T>::step(B, c->p.order, c->p.flux, KIND_T3B, c->stream);
+    if (c->fast) {
+        const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs3[1].data());
+        e = Launch<T, T>::step_fast3(B, cf, vortex_factors<T>(c, t + dt / 3.0, t, t + 0.75 * dt), c->tmX[1],
+                                     c->tmPhi[c->pr[1]], c->p.order, c->p.flux, KIND_T3B, c->stream);
+    } else {
+        e = Launch<T, T>::step(B, c->p.order, c->p.flux, KIND_T3B, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "three-stage kernel B");
     std::swap(c->pr[0], c->pr[1]);
     return DUGKS_OK;
@@ -437,9 +473,11 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     c->plane = (size_t)(p->ny + 2 * GHOST) * c->pitch;
     c->nsets = p->stages == 3 ? 3 : 2;
     c->nphi = p->precision == DUGKS_FP16F ? 3 : 2;
-    // the TMA-staged kernel serves the two-stage scheme at orders 2 and 3
-    c->fast = p->stages == 2 && p->order <= 3 && encode_fn() != nullptr;
-    if (c->fast) {
+    // the TMA-staged kernels serve orders 2 and 3 (three-stage: full storage, one tile shape)
+    c->fast = p->order <= 3 && (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
+    if (c->fast && p->stages == 3) {
+        c->variant = 2;
+    } else if (c->fast) {
         // measured (FP32, L2 flushed between steps): 8 warps x 2 rows per thread fastest
         // on grids that fill about one wave of tiles (256^2), 8 x 3 from 1024^2 up
         c->variant = (int64_t)p->nx * p->ny >= 512 * 512 ? 4 : 2;
@@ -618,8 +656,10 @@ int dugks_status(dugks_ctx *c) {
 
 int dugks_set_variant(dugks_ctx *c, int variant) {
     if (!c || variant < -1 || variant >= FAST_VARIANTS) return DUGKS_EINVAL;
-    const bool fast_capable = c->p.stages == 2 && c->p.order <= 3 && encode_fn() != nullptr;
-    if (!fast_capable) return DUGKS_OK;   // only the two-stage order-2/3 path has variants
+    const bool fast_capable = c->p.order <= 3 && (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) &&
+                              encode_fn() != nullptr;
+    if (!fast_capable) return DUGKS_OK;   // order 4 always runs the generic kernel
+    if (c->p.stages == 3 && variant >= 0) variant = 2;   // the three-stage kernels have one tile shape
     cudaSetDevice(c->dev);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");

@@ -161,7 +161,7 @@ __device__ __noinline__ void put_ghosts9(const StepParams<T> &p, V *out, int x, 
             out[6 * pl + g] = v6;
             out[7 * pl + g] = v7;
             out[8 * pl + g] = v8;
-            p.phi_out[g] = phi;
+            if (p.phi_out != nullptr) p.phi_out[g] = phi;
         }
     }
 }
@@ -206,13 +206,19 @@ struct FastTile {
     static constexpr int cmin(int a, int b) { return a < b ? a : b; }
     static constexpr int min_blocks =
         cmin(cmin((int)((228u * 1024u) / (smem_bytes + 1024u)), 2048 / NT), 65536 / (NT * 64));
+    // first kernel of the three-stage scheme: a second per-direction partial (the
+    // accumulator output) after the common layout
+    static constexpr size_t oPart2 = al(smem_bytes);
+    static constexpr size_t smem_bytes_t3a = oPart2 + sizeof(T) * 9 * 32 * (TY + 1);
+    static constexpr int min_blocks_t3a =
+        cmin(cmin((int)((228u * 1024u) / (smem_bytes_t3a + 1024u)), 2048 / NT), 65536 / (NT * 64));
 };
 
 // One tile (bx, by) of one grid. The caller initialised the mbarrier `bar`
 // (count 1) and passes the parity of its next phase. Returns false if the TMA
 // copy never arrived (status flagged). mass_out: where the tile's FP64 partial
 // goes (may be null).
-template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR, int KIND = KIND_T2>
 __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe_,
                                           const CUtensorMap *tmX, const CUtensorMap *tmPo, const CUtensorMap *tmPc,
                                           int bx, int by, double *mass_out, unsigned char *smem, uint64_t *bar,
@@ -222,6 +228,13 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     constexpr int NT = FT::NT, BW = FT::BW, BWT = FT::BWT, RH = FT::RH, NE = FT::NE, NXS = FT::NXS;
     constexpr bool DEV = FT::DEV;
     static_assert(ORDER == 2 || ORDER == 3, "fast path covers orders 2 and 3");
+    // KIND_T2: the two-stage step. KIND_T3A / KIND_T3B: the two kernels of the
+    // three-stage step (Sec. II.B.2), full storage only:
+    //   T3A  out1 = X + be1 (g - X) + ga1 L (tilde f at t'), out2 = X + be2 (g - X) + ga2 L
+    //        (the accumulator, in T), phi_out = phi of X;
+    //   T3B  out1 = acc + be1 (g - X) + ga1 L (hat f at t_n + dt; al1 = -be1), mass partial.
+    static_assert(KIND == KIND_T2 || !DEV, "the three-stage scheme keeps full values");
+    constexpr bool T3A = KIND == KIND_T3A, T3B = KIND == KIND_T3B;
 
     ST *sX = reinterpret_cast<ST *>(smem + FT::oX);
     T *sPo = reinterpret_cast<T *>(smem + FT::oPo);
@@ -405,6 +418,10 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         if constexpr (DEV) return sPart[(k * (TY + 1) + (fy0 + 1 + r)) * 32 + lane];
         else return reinterpret_cast<T *>(sX)[k * RH * BW + xbase + r * BW];
     };
+    // T3A: the accumulator's partial
+    T *sPart2 = reinterpret_cast<T *>(smem + FT::oPart2);
+    auto part2_ref = [&](int k, int r) -> T & { return sPart2[(k * (TY + 1) + (fy0 + 1 + r)) * 32 + lane]; };
+    const T gmc2 = p.ga2 * (T(1) - p.c2);
 
     // The direction loop is unrolled: xi_k, w_k, the stencil coefficients (kernel
     // parameters, i.e. constant-bank operands) and the structural zeros of each
@@ -451,6 +468,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             const T below = sNB[((k - 1) & 1) * NW * 32 + (warp > 0 ? warp - 1 : 0) * 32 + lane];
             const T d = ey(k - 1) > 0 ? (fn0Prev - below) : (below - fn0Prev);
             part_ref(k - 1, 0) -= gmc * d;
+            if constexpr (T3A) part2_ref(k - 1, 0) -= gmc2 * d;
             sumD[0] += d;
         }
         // S3b: face values of my MR cells from a (MR + 3) x 4 window of bar f^+_k
@@ -493,7 +511,8 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
                 }
                 if (ky != 0 && r > 0) d = ky > 0 ? d + (fn[r] - fn[r - 1]) : d - (fn[r] - fn[r - 1]);
                 // cells outside the tile write harmless values
-                part_ref(k, r) = xk[r] + p.be1 * (gk[r] - xk[r]) - gmc * d;
+                part_ref(k, r) = (T3B ? T(0) : xk[r]) + p.be1 * (gk[r] - xk[r]) - gmc * d;
+                if constexpr (T3A) part2_ref(k, r) = xk[r] + p.be2 * (gk[r] - xk[r]) - gmc2 * d;
                 sumD[r] += d;
             }
         }
@@ -506,6 +525,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         const T below = sNB[(8 & 1) * NW * 32 + (warp > 0 ? warp - 1 : 0) * 32 + lane];
         const T d = ey(8) > 0 ? (fn0Prev - below) : (below - fn0Prev);
         part_ref(8, 0) -= gmc * d;
+        if constexpr (T3A) part2_ref(8, 0) -= gmc2 * d;
         sumD[0] += d;
     }
 
@@ -547,6 +567,61 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         // Delta V_b = (V(c + E) - V(c - E)) / 2 and likewise north
         const T dVEx = T(0.5) * (sV[cj + 1] - sV[cj - 1]), dVEy = T(0.5) * (sV[NC + cj + 1] - sV[NC + cj - 1]);
         const T dVNx = T(0.5) * (sV[cj + CW] - sV[cj - CW]), dVNy = T(0.5) * (sV[NC + cj + CW] - sV[NC + cj - CW]);
+        if constexpr (KIND != KIND_T2) {
+            // out = part_k - w_k (xi_x A1 + xi_y A2 + xi_x^2 B1 + xi_x xi_y B2 + xi_y^2 B3), all scaled
+            // by the output's gamma; its rest component from phi_base + gamma sum_k L_k
+            auto combine = [&](T gam, T gmcX, T phib, auto part, T (&o)[9]) -> T {
+                const T g2 = gam * p.c2, g3 = gam * p.c3;
+                const T A1 = g2 * dE[0], A2 = g2 * dN[0];
+                const T B1 = T(3) * g2 * dE[1] + g3 * dVEx;
+                const T B2 = T(3) * g2 * (dE[2] + dN[1]) + g3 * (dVEy + dVNx);
+                const T B3 = T(3) * g2 * dN[2] + g3 * dVNy;
+                const T ph = phib - gmcX * sumD[r] - (B1 + B3) * T(1.0 / 3.0);
+                const T S13 = B1 + B3;
+                o[1] = part(1) - wq<T>(1) * (A1 + B1);
+                o[5] = part(5) - wq<T>(5) * (B1 - A1);
+                o[3] = part(3) - wq<T>(3) * (A2 + B3);
+                o[7] = part(7) - wq<T>(7) * (B3 - A2);
+                o[2] = part(2) - wq<T>(2) * ((A1 + A2) + (S13 + B2));
+                o[4] = part(4) - wq<T>(4) * ((A2 - A1) + (S13 - B2));
+                o[6] = part(6) - wq<T>(6) * ((S13 + B2) - (A1 + A2));
+                o[8] = part(8) - wq<T>(8) * ((A1 - A2) + (S13 - B2));
+                T rsum = T(0);
+#pragma unroll
+                for (int k = 1; k < 9; k++) rsum += o[k];
+                o[0] = ph - rsum;
+                return ph;
+            };
+            const bool edge = gx < GHOST || gx >= nx - GHOST || gy < GHOST || gy >= ny - GHOST;
+            const size_t g = gidx(p, gx, gy);
+            T *O = static_cast<T *>(p.out1);
+            T o[9];
+            if constexpr (T3A) {
+                combine(p.ga1, gmc, cg[r], [&](int k) { return part_ref(k, r); }, o);
+#pragma unroll
+                for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
+                p.phi_out[g] = cg[r];
+                if (edge) put_ghosts9(p, O, gx, gy, cg[r], o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
+                T o2[9];
+                combine(p.ga2, gmc2, cg[r], [&](int k) { return part2_ref(k, r); }, o2);
+#pragma unroll
+                for (int k = 0; k < 9; k++) p.out2[k * plane + g] = o2[k];   // read per cell only: no ghosts
+            } else {
+                const T *Acc = static_cast<const T *>(p.acc);
+                T a[9], pha = T(0);
+#pragma unroll
+                for (int k = 0; k < 9; k++) {
+                    a[k] = Acc[k * plane + g];
+                    pha += a[k];
+                }
+                const T phn = combine(p.ga1, gmc, pha, [&](int k) { return a[k] + part_ref(k, r); }, o);
+#pragma unroll
+                for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
+                if (edge) put_ghosts9(p, O, gx, gy, phn, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
+                msum += (double)phn;
+            }
+            continue;
+        }
         // gamma w_k (c2 Phi_k + c3 Psi_k) = w_k (xi_x A1 + xi_y A2 + xi_x^2 B1 + xi_x xi_y B2 + xi_y^2 B3)
         const T A1 = gc2 * dE[0], A2 = gc2 * dN[0];
         const T B1 = T(3) * gc2 * dE[1] + gc3 * dVEx;
@@ -604,8 +679,9 @@ __device__ __forceinline__ uint64_t *fast_bar(unsigned char *smem) {
 }
 
 // One grid, one tile per CTA.
-template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
-__global__ void __launch_bounds__(NW * 32, (FastTile<T, ST, NW, MR>::min_blocks))
+template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR, int KIND = KIND_T2>
+__global__ void __launch_bounds__(NW * 32, (KIND == KIND_T3A ? FastTile<T, ST, NW, MR>::min_blocks_t3a
+                                                             : FastTile<T, ST, NW, MR>::min_blocks))
 step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant__ FaceCoefs<T> cf,
                  const __grid_constant__ FastExtra<T> fe_, const __grid_constant__ CUtensorMap tmX,
                  const __grid_constant__ CUtensorMap tmPo, const __grid_constant__ CUtensorMap tmPc) {
@@ -614,7 +690,8 @@ step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant_
     if (threadIdx.x == 0) mbar_init(bar, 1);
     pdl_wait();   // the previous kernel's output (launched with programmatic serialization)
     double *mo = p.mass_partial ? p.mass_partial + blockIdx.y * p.tiles_x + blockIdx.x : nullptr;
-    fast_tile<T, ST, ORDER, FLUX, NW, MR>(p, cf, fe_, &tmX, &tmPo, &tmPc, blockIdx.x, blockIdx.y, mo, smem, bar, 0);
+    fast_tile<T, ST, ORDER, FLUX, NW, MR, KIND>(p, cf, fe_, &tmX, &tmPo, &tmPc, blockIdx.x, blockIdx.y, mo, smem, bar,
+                                                0);
     // the next kernel may be scheduled once every tile is done with its work (a
     // trigger at entry would place its waiting CTAs while this grid still runs,
     // unevenly when the grid is a single wave)

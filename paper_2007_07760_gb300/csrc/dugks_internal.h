@@ -42,6 +42,11 @@ struct Launch {
     static cudaError_t step_fast(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
                                  const CUtensorMap &tmPo, const CUtensorMap &tmPc, int order, int flux,
                                  int variant, cudaStream_t s);
+    // one kernel of the three-stage step (kind KIND_T3A or KIND_T3B) on the TMA-staged
+    // path, tile 8 warps x 2 rows (full storage only: ST == T)
+    static cudaError_t step_fast3(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,
+                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, int order, int flux, int kind,
+                                  cudaStream_t s);
 };
 
 template <typename T>

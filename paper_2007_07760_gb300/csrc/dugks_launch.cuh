@@ -145,6 +145,51 @@ cudaError_t Launch<T, ST>::step_fast(const StepParams<T> &p, const FaceCoefs<T> 
     return cudaErrorInvalidValue;
 }
 
+template <typename T, int ORDER, int FLUX, int KIND>
+static cudaError_t launch_fast3_t(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,
+                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, cudaStream_t s) {
+    using FT = FastTile<T, T, 8, 2>;
+    constexpr size_t smem = KIND == KIND_T3A ? FT::smem_bytes_t3a : FT::smem_bytes;
+    auto kern = step_fast_kernel<T, T, ORDER, FLUX, 8, 2, KIND>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nx + FT::TX - 1) / FT::TX, (p.ny + FT::TY - 1) / FT::TY);
+    cfg.blockDim = dim3(FT::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p, cf, fe, tmX, tmPo, tmPo);
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::step_fast3(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,
+                                      const CUtensorMap &tmX, const CUtensorMap &tmPo, int order, int flux, int kind,
+                                      cudaStream_t s) {
+#define DUGKS_T3(O, F)                                                                       \
+    return kind == KIND_T3A ? launch_fast3_t<T, O, F, KIND_T3A>(p, cf, fe, tmX, tmPo, s)      \
+                            : launch_fast3_t<T, O, F, KIND_T3B>(p, cf, fe, tmX, tmPo, s)
+    if (kind != KIND_T3A && kind != KIND_T3B) return cudaErrorInvalidValue;
+    if (order == 2) {
+        if (flux == 0) DUGKS_T3(2, 0);
+        DUGKS_T3(2, 1);
+    }
+    if (order == 3) {
+        if (flux == 0) DUGKS_T3(3, 0);
+        DUGKS_T3(3, 1);
+    }
+#undef DUGKS_T3
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, typename ST>
 cudaError_t Launch<T, ST>::phi(const StepParams<T> &p, T *out, cudaStream_t s) {
     dim3 block(128), grid((p.nx + 127) / 128, p.ny);
