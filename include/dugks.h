@@ -129,9 +129,8 @@ const char *dugks_last_error(const dugks_ctx *c);
  * cells high). The default is 2 below 512 x 512 cells and 4 from there up; -1
  * selects the generic fused kernel (one thread per cell and stage, no TMA), the
  * plain comparison path. A tuning choice only: results agree to rounding.
- * Returns DUGKS_EINVAL for any other number. The three-stage scheme's two
- * TMA-staged kernels have one tile shape (8 x 2): any variant >= 0 selects them.
- * Ignored for order 4, which always uses the generic kernel.
+ * Returns DUGKS_EINVAL for any other number. Order 4 and the three-stage
+ * scheme have one TMA-staged tile shape each (8 x 2): any variant >= 0 selects it.
  * dugks_get_variant returns -1 when the context uses the generic kernel. */
 int dugks_set_variant(dugks_ctx *c, int variant);
 int dugks_get_variant(const dugks_ctx *c);

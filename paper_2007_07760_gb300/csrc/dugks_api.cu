@@ -137,7 +137,7 @@ bool encode_map(CUtensorMap *m, void *base, size_t es, bool half, const dugks_ct
 
 template <typename T, typename ST>
 bool setup_fast(dugks_ctx *c) {
-    const FastGeom g = Launch<T, ST>::fast_geom(c->variant);
+    const FastGeom g = Launch<T, ST>::fast_geom(c->variant, c->p.order);
     const bool half = Store<T, ST>::deviation;
     for (int s = 0; s < 2; s++)
         if (!encode_map(&c->tmX[s], c->X[s], sizeof(ST), half, c, 9, g.box_w, g.box_h)) return false;
@@ -175,6 +175,20 @@ int ensure_init(dugks_ctx *c) {
     }
 }
 
+// Single-vortex reversal factors cos(pi t / T) at the cell time, the older time
+// of d(phi u)/dt and the face time (FP64 on the host); zero for other velocities.
+template <typename T>
+FastExtra<T> vortex_factors(const dugks_ctx *c, double t, double t_old, double t_face) {
+    FastExtra<T> fx{};
+    if (c->vel_kind == DUGKS_VEL_VORTEX) {
+        const double PI = 3.14159265358979323846, Tp = c->vel[2];
+        fx.vc_t = (T)std::cos(PI * t / Tp);
+        fx.vc_told = (T)std::cos(PI * t_old / Tp);
+        fx.vc_tface = (T)std::cos(PI * t_face / Tp);
+    }
+    return fx;
+}
+
 // One two-stage step. Full storage: X[cur] -> X[1-cur]; phi[pr0] holds
 // phi^{n-1}, phi[pr1] receives phi^n. Deviation storage: phi[pr0] = phi^n
 // (of X), phi[pr1] = phi^{n-1}, phi[pr2] receives phi^{n+1}.
@@ -209,7 +223,17 @@ int step_t2(dugks_ctx *c) {
     q.phi_old = static_cast<const T *>(c->phi[iPo]);
     q.phi_out = static_cast<T *>(c->phi[iOut]);
     cudaError_t e;
-    if (c->fast) {
+    if (c->fast && c->p.order == 4) {
+        if (c->coef_h != h) {
+            const FaceCoefs<T, 2> cf = make_face_coefs_r<T, 2>(4, c->p.flux, h);
+            c->coefs.assign(reinterpret_cast<const unsigned char *>(&cf),
+                            reinterpret_cast<const unsigned char *>(&cf) + sizeof cf);
+            c->coef_h = h;
+        }
+        e = Launch<T, ST>::step_fast4(q, *reinterpret_cast<const FaceCoefs<T, 2> *>(c->coefs.data()),
+                                      vortex_factors<T>(c, t, t - dt, t + h), c->tmX[c->cur], c->tmPhi[iPo],
+                                      c->tmPhi[iPc], c->p.flux, KIND_T2, c->stream);
+    } else if (c->fast) {
         if (c->coef_h != h) {
             FaceCoefs<T> cf = make_face_coefs<T>(c->p.order, c->p.flux, h);
             c->coefs.assign(reinterpret_cast<unsigned char *>(&cf), reinterpret_cast<unsigned char *>(&cf) + sizeof cf);
@@ -237,20 +261,6 @@ int step_t2(dugks_ctx *c) {
         std::swap(c->pr[0], c->pr[1]);
     }
     return DUGKS_OK;
-}
-
-// Single-vortex reversal factors cos(pi t / T) at the cell time, the older time
-// of d(phi u)/dt and the face time (FP64 on the host); zero for other velocities.
-template <typename T>
-FastExtra<T> vortex_factors(const dugks_ctx *c, double t, double t_old, double t_face) {
-    FastExtra<T> fx{};
-    if (c->vel_kind == DUGKS_VEL_VORTEX) {
-        const double PI = 3.14159265358979323846, Tp = c->vel[2];
-        fx.vc_t = (T)std::cos(PI * t / Tp);
-        fx.vc_told = (T)std::cos(PI * t_old / Tp);
-        fx.vc_tface = (T)std::cos(PI * t_face / Tp);
-    }
-    return fx;
 }
 
 // One three-stage step (Sec. II.B.2): X[0] = hat f, X[1] = tilde f at t',
@@ -283,13 +293,23 @@ int step_t3(dugks_ctx *c) {
     A.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
     cudaError_t e;
     if (c->fast && c->coef3_dt != dt) {
-        const FaceCoefs<T> ca = make_face_coefs<T>(c->p.order, c->p.flux, dt / 6.0);
-        const FaceCoefs<T> cb = make_face_coefs<T>(c->p.order, c->p.flux, 5.0 * dt / 12.0);
-        c->coefs3[0].assign(reinterpret_cast<const unsigned char *>(&ca), reinterpret_cast<const unsigned char *>(&ca) + sizeof ca);
-        c->coefs3[1].assign(reinterpret_cast<const unsigned char *>(&cb), reinterpret_cast<const unsigned char *>(&cb) + sizeof cb);
+        auto keep = [](std::vector<unsigned char> &v, const auto &cf) {
+            v.assign(reinterpret_cast<const unsigned char *>(&cf), reinterpret_cast<const unsigned char *>(&cf) + sizeof cf);
+        };
+        if (c->p.order == 4) {
+            keep(c->coefs3[0], make_face_coefs_r<T, 2>(4, c->p.flux, dt / 6.0));
+            keep(c->coefs3[1], make_face_coefs_r<T, 2>(4, c->p.flux, 5.0 * dt / 12.0));
+        } else {
+            keep(c->coefs3[0], make_face_coefs<T>(c->p.order, c->p.flux, dt / 6.0));
+            keep(c->coefs3[1], make_face_coefs<T>(c->p.order, c->p.flux, 5.0 * dt / 12.0));
+        }
         c->coef3_dt = dt;
     }
-    if (c->fast) {
+    if (c->fast && c->p.order == 4) {
+        e = Launch<T, T>::step_fast4(A, *reinterpret_cast<const FaceCoefs<T, 2> *>(c->coefs3[0].data()),
+                                     vortex_factors<T>(c, t, t - dt, t + dt / 6.0), c->tmX[0], c->tmPhi[c->pr[0]],
+                                     c->tmPhi[c->pr[0]], c->p.flux, KIND_T3A, c->stream);
+    } else if (c->fast) {
         const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs3[0].data());
         e = Launch<T, T>::step_fast3(A, cf, vortex_factors<T>(c, t, t - dt, t + dt / 6.0), c->tmX[0],
                                      c->tmPhi[c->pr[0]], c->p.order, c->p.flux, KIND_T3A, c->stream);
@@ -317,7 +337,11 @@ int step_t3(dugks_ctx *c) {
     B.out1 = c->X[0];
     B.phi_old = static_cast<const T *>(c->phi[c->pr[1]]);
     B.mass_partial = c->partial;
-    if (c->fast) {
+    if (c->fast && c->p.order == 4) {
+        e = Launch<T, T>::step_fast4(B, *reinterpret_cast<const FaceCoefs<T, 2> *>(c->coefs3[1].data()),
+                                     vortex_factors<T>(c, t + dt / 3.0, t, t + 0.75 * dt), c->tmX[1],
+                                     c->tmPhi[c->pr[1]], c->tmPhi[c->pr[1]], c->p.flux, KIND_T3B, c->stream);
+    } else if (c->fast) {
         const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs3[1].data());
         e = Launch<T, T>::step_fast3(B, cf, vortex_factors<T>(c, t + dt / 3.0, t, t + 0.75 * dt), c->tmX[1],
                                      c->tmPhi[c->pr[1]], c->p.order, c->p.flux, KIND_T3B, c->stream);
@@ -473,9 +497,10 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     c->plane = (size_t)(p->ny + 2 * GHOST) * c->pitch;
     c->nsets = p->stages == 3 ? 3 : 2;
     c->nphi = p->precision == DUGKS_FP16F ? 3 : 2;
-    // the TMA-staged kernels serve orders 2 and 3 (three-stage: full storage, one tile shape)
-    c->fast = p->order <= 3 && (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
-    if (c->fast && p->stages == 3) {
+    // the TMA-staged kernels serve every order and both schemes (three-stage: full
+    // storage; order 4 and the three-stage scheme: one tile shape, 8 x 2)
+    c->fast = (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
+    if (c->fast && (p->stages == 3 || p->order == 4)) {
         c->variant = 2;
     } else if (c->fast) {
         // measured (FP32, L2 flushed between steps): 8 warps x 2 rows per thread fastest
@@ -656,10 +681,10 @@ int dugks_status(dugks_ctx *c) {
 
 int dugks_set_variant(dugks_ctx *c, int variant) {
     if (!c || variant < -1 || variant >= FAST_VARIANTS) return DUGKS_EINVAL;
-    const bool fast_capable = c->p.order <= 3 && (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) &&
-                              encode_fn() != nullptr;
-    if (!fast_capable) return DUGKS_OK;   // order 4 always runs the generic kernel
-    if (c->p.stages == 3 && variant >= 0) variant = 2;   // the three-stage kernels have one tile shape
+    const bool fast_capable = (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) && encode_fn() != nullptr;
+    if (!fast_capable) return DUGKS_OK;
+    // order 4 and the three-stage kernels have one tile shape
+    if ((c->p.stages == 3 || c->p.order == 4) && variant >= 0) variant = 2;
     cudaSetDevice(c->dev);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");

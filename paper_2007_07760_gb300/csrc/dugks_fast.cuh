@@ -28,26 +28,32 @@
 
 namespace dugks {
 
-// Face stencils of one reconstruction time h: east face of cell c over rows
-// -1..1 and columns -1..2 around c, north face over rows -1..2, columns -1..1
-// (stored with a zero fourth column).
-template <typename T>
+// Face stencils of one reconstruction time h, for stencils of radius R (1 for
+// orders 2 and 3, 2 for order 4): east face of cell c over rows -R..R and
+// columns -R..R+1 around c, north face over rows -R..R+1 and columns -R..R
+// (stored with a zero last column). Index = offset + R.
+template <typename T, int R = 1>
 struct FaceCoefs {
-    T e[9][3][4];
-    T n[9][4][4];
+    T e[9][2 * R + 1][2 * R + 2];
+    T n[9][2 * R + 2][2 * R + 2];
 };
 
 // structural non-zeros of the face stencils (the host fills the same pattern);
-// b, a are row and column offsets from the face-owner cell
-__host__ __device__ constexpr bool tapE(int flux, int k, int b, int a) {
-    // b in -1..1, a in -1..2
-    return flux == 0 ? (ex(k) > 0 ? a <= 1 : ex(k) < 0 ? a >= 0 : true)
-                     : (ey(k) == 0 ? (b == 0 && (a == 0 || a == 1)) : (b != 0 || a == 0 || a == 1));
+// b, a are row and column offsets from the face-owner cell. Upwind: the taps of
+// the expansion cell (c or its east / north neighbour, both for a tie). Central:
+// the two face cells, plus the tangential derivatives when xi has a tangential part
+// (radius 2: the whole box).
+__host__ __device__ constexpr bool tapE(int flux, int k, int b, int a, int R = 1) {
+    // b in -R..R, a in -R..R+1
+    return flux == 0 ? (ex(k) > 0 ? a <= R : ex(k) < 0 ? a >= 1 - R : true)
+                     : (ey(k) == 0 ? (b == 0 && (a == 0 || a == 1))
+                                   : (R > 1 || b != 0 || a == 0 || a == 1));
 }
-__host__ __device__ constexpr bool tapN(int flux, int k, int b, int a) {
-    // b in -1..2, a in -1..1
-    return flux == 0 ? (ey(k) > 0 ? b <= 1 : ey(k) < 0 ? b >= 0 : true)
-                     : (ex(k) == 0 ? (a == 0 && (b == 0 || b == 1)) : (a != 0 || b == 0 || b == 1));
+__host__ __device__ constexpr bool tapN(int flux, int k, int b, int a, int R = 1) {
+    // b in -R..R+1, a in -R..R
+    return flux == 0 ? (ey(k) > 0 ? b <= R : ey(k) < 0 ? b >= 1 - R : true)
+                     : (ex(k) == 0 ? (a == 0 && (b == 0 || b == 1))
+                                   : (R > 1 || a != 0 || b == 0 || b == 1));
 }
 
 // Per-step scalars of the fast kernel that the generic parameters do not carry.
@@ -166,16 +172,19 @@ __device__ __noinline__ void put_ghosts9(const StepParams<T> &p, V *out, int x, 
     }
 }
 
-template <typename T, typename ST, int NW, int MR>
+// Tile of the TMA-staged kernel for stencils of radius R: state region with a
+// halo of H = 1 + 2R, cell-quantity region (bar f^+, V) with a halo of R + 1.
+template <typename T, typename ST, int NW, int MR, int R = 1>
 struct FastTile {
     static constexpr int NT = NW * 32;
+    static constexpr int H = 1 + 2 * R, C1 = R + 1;
     static constexpr int TX = 31, TY = NW * MR - 1;         // cells written
-    static constexpr int RW = TX + 6, RH = TY + 6;          // state region: halo 3
-    static constexpr int CW = TX + 4, CH = TY + 4;          // cell-quantity region: halo 2
+    static constexpr int RW = TX + 2 * H, RH = TY + 2 * H;  // state region
+    static constexpr int CW = TX + 2 * C1, CH = TY + 2 * C1;   // cell-quantity region
     static constexpr int NC = CW * CH;
-    // cell-quantity cells not owned by a thread: columns -2, TX, TX + 1 (all rows)
-    // and rows -2, TY, TY + 1 (columns -1 .. TX - 1)
-    static constexpr int NE = 3 * CH + 3 * 32;
+    // cell-quantity cells not owned by a thread: columns -R-1 .. -2 and TX .. TX + R
+    // (all rows), rows -R-1 .. -2 and TY .. TY + R (columns -1 .. TX - 1)
+    static constexpr int NE = (2 * R + 1) * (CH + 32);
     static constexpr int NXS = (NE + NT - 1) / NT;          // extra slots per thread
     static constexpr int AS = 16 / (int)sizeof(ST);         // TMA x alignment of the state (elements)
     static constexpr int AT = 16 / (int)sizeof(T);          // ... of the phi planes
@@ -219,15 +228,18 @@ struct FastTile {
 // copy never arrived (status flagged). mass_out: where the tile's FP64 partial
 // goes (may be null).
 template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR, int KIND = KIND_T2>
-__device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe_,
+__device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoefs<T, (ORDER == 4 ? 2 : 1)> &cf,
+                                          const FastExtra<T> &fe_,
                                           const CUtensorMap *tmX, const CUtensorMap *tmPo, const CUtensorMap *tmPc,
                                           int bx, int by, double *mass_out, unsigned char *smem, uint64_t *bar,
                                           uint32_t phase) {
-    using FT = FastTile<T, ST, NW, MR>;
+    constexpr int R = ORDER == 4 ? 2 : 1;   // stencil radius
+    using FT = FastTile<T, ST, NW, MR, R>;
     constexpr int TX = FT::TX, TY = FT::TY, RW = FT::RW, CW = FT::CW, CH = FT::CH, NC = FT::NC;
     constexpr int NT = FT::NT, BW = FT::BW, BWT = FT::BWT, RH = FT::RH, NE = FT::NE, NXS = FT::NXS;
+    constexpr int H = FT::H, C1 = FT::C1;
     constexpr bool DEV = FT::DEV;
-    static_assert(ORDER == 2 || ORDER == 3, "fast path covers orders 2 and 3");
+    static_assert(ORDER >= 2 && ORDER <= 4, "stencil orders 2 to 4");
     // KIND_T2: the two-stage step. KIND_T3A / KIND_T3B: the two kernels of the
     // three-stage step (Sec. II.B.2), full storage only:
     //   T3A  out1 = X + be1 (g - X) + ga1 L (tilde f at t'), out2 = X + be2 (g - X) + ga2 L
@@ -251,8 +263,8 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = p.nx, ny = p.ny;
     const int x0 = bx * TX, y0 = by * TY;
-    // padded-plane coordinates of the state box; ox = offset of relative x = -3 in the box
-    const int xs_raw = x0 - 3 + GHOST, ys = y0 - 3 + GHOST;
+    // padded-plane coordinates of the state box; ox = offset of relative x = -H in the box
+    const int xs_raw = x0 - H + GHOST, ys = y0 - H + GHOST;
     const int xs = xs_raw / FT::AS * FT::AS, ox = xs_raw - xs;
     const int xst = xs_raw / FT::AT * FT::AT, oxt = xs_raw - xst;
 
@@ -270,7 +282,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     // while the copy is in flight: velocity tables
     // single vortex u = -U A(x) B(y) c(t), v = U A(y) B(x) c(t), with
     // A(s) = sin^2(pi s / L), B(s) = sin(2 pi s / L) at cell centres (s = i + 1/2)
-    // and at faces (s = i + 1) of the wrapped cells of this tile (+2 halo)
+    // and at faces (s = i + 1) of the wrapped cells of this tile (+ R + 1 halo)
     T *sAxc = sVel, *sBxc = sAxc + CW, *sAxf = sBxc + CW, *sBxf = sAxf + CW;
     T *sAyc = sBxf + CW, *sByc = sAyc + CH, *sAyf = sByc + CH, *sByf = sAyf + CH;
     if (p.vel_kind == VEL_VORTEX) {
@@ -279,7 +291,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             const bool isx = i < 2 * CW;
             const int j = isx ? (i >> 1) : ((i - 2 * CW) >> 1);
             const bool face = (i & 1) != 0;
-            const int g = isx ? wrap_small(x0 + j - 2, nx) : wrap_small(y0 + j - 2, ny);
+            const int g = isx ? wrap_small(x0 + j - C1, nx) : wrap_small(y0 + j - C1, ny);
             const T s = T(g) + (face ? T(1) : T(0.5));
             const T sn = sinpi_(s / L);
             const T A = sn * sn, B = sinpi_(T(2) * s / L);
@@ -301,10 +313,10 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     }
 
     // accessors (relative cell coordinates x, y of the tile)
-    auto xidx = [&](int x, int y) { return (y + 3) * BW + (x + 3 + ox); };   // + k * RH * BW
+    auto xidx = [&](int x, int y) { return (y + H) * BW + (x + H + ox); };   // + k * RH * BW
     auto PHI = [&](int x, int y) -> T {
-        if constexpr (DEV) return sPc[(y + 3) * BWT + (x + 3 + oxt)];
-        else return sPhi[(y + 3) * RW + (x + 3)];
+        if constexpr (DEV) return sPc[(y + H) * BWT + (x + H + oxt)];
+        else return sPhi[(y + H) * RW + (x + H)];
     };
     // velocity of a cell centre (where = 0), east face (1) or north face (2)
     auto vel = [&](int x, int y, int where, T t, T vc, T &u, T &v) {
@@ -312,7 +324,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             u = p.vp0;
             v = p.vp1;
         } else if (p.vel_kind == VEL_VORTEX) {
-            const int i = x + 2, j = y + 2;
+            const int i = x + C1, j = y + C1;
             const T Ax = where == 1 ? sAxf[i] : sAxc[i], Bx = where == 1 ? sBxf[i] : sBxc[i];
             const T Ay = where == 2 ? sAyf[j] : sAyc[j], By = where == 2 ? sByf[j] : sByc[j];
             u = -p.vp1 * Ax * By * vc;
@@ -327,9 +339,15 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     // and V = theta n + 3 D into shared memory (face sources)
     auto cell_q = [&](int x, int y, T &ph, T &Px, T &Py) {
         ph = PHI(x, y);
-        const T ne = PHI(x + 1, y + 1), nw = PHI(x - 1, y + 1), se = PHI(x + 1, y - 1), sw = PHI(x - 1, y - 1);
-        const T gxp = (PHI(x + 1, y) - PHI(x - 1, y)) * T(1.0 / 3.0) + ((ne - nw) + (se - sw)) * T(1.0 / 12.0);
-        const T gyp = (PHI(x, y + 1) - PHI(x, y - 1)) * T(1.0 / 3.0) + ((ne - se) + (nw - sw)) * T(1.0 / 12.0);
+        T gxp, gyp;
+        if constexpr (ORDER == 4) {   // the order's own gradient (Sec. II.B.1)
+            if constexpr (DEV) grad21(sPc + (y + H) * BWT + (x + H + oxt), BWT, gxp, gyp);
+            else grad21(sPhi + (y + H) * RW + (x + H), RW, gxp, gyp);
+        } else {
+            const T ne = PHI(x + 1, y + 1), nw = PHI(x - 1, y + 1), se = PHI(x + 1, y - 1), sw = PHI(x - 1, y - 1);
+            gxp = (PHI(x + 1, y) - PHI(x - 1, y)) * T(1.0 / 3.0) + ((ne - nw) + (se - sw)) * T(1.0 / 12.0);
+            gyp = (PHI(x, y + 1) - PHI(x, y - 1)) * T(1.0 / 3.0) + ((ne - se) + (nw - sw)) * T(1.0 / 12.0);
+        }
         const T g2 = gxp * gxp + gyp * gyp;
         T nxv = T(0), nyv = T(0);
         if (g2 > T(1e-24)) {  // Eq. (2); n = 0 where grad phi vanishes
@@ -344,27 +362,27 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         if (p.useD) {  // d(phi u)/dt, backward difference
             T uo, vo;
             vel(x, y, 0, p.t_old, fe_.vc_told, uo, vo);
-            const T po = sPo[(y + 3) * BWT + (x + 3 + oxt)];
+            const T po = sPo[(y + H) * BWT + (x + H + oxt)];
             Dx = (ph * u - po * uo) * p.inv_dtD;
             Dy = (ph * v - po * vo) * p.inv_dtD;
         }
         const T Vx = theta * nxv + T(3) * Dx, Vy = theta * nyv + T(3) * Dy;  // Eq. (14b)
         Px = T(3) * ph * u + p.tau * Vx;
         Py = T(3) * ph * v + p.tau * Vy;
-        const int j = (y + 2) * CW + (x + 2);
+        const int j = (y + C1) * CW + (x + C1);
         sV[j] = Vx;
         sV[NC + j] = Vy;
     };
 
     // ---- S1: phi = sum_k X_k on the state region (Eq. (30)) ------------------
     if constexpr (!DEV) {
-        for (int y = warp - 3; y < RH - 3; y += NW)
-            for (int x = lane - 3; x < RW - 3; x += 32) {
+        for (int y = warp - H; y < RH - H; y += NW)
+            for (int x = lane - H; x < RW - H; x += 32) {
                 const int xi = xidx(x, y);
                 T s = T(0);
 #pragma unroll
                 for (int k = 0; k < 9; k++) s += (T)sX[k * RH * BW + xi];
-                sPhi[(y + 3) * RW + (x + 3)] = s;
+                sPhi[(y + H) * RW + (x + H)] = s;
             }
     }
     __syncthreads();
@@ -390,16 +408,16 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         if (!exw[s]) continue;
         const int e = min(tid + s * NT, NE - 1);
         int x, y;
-        if (e < 3 * CH) {
-            const int c = e / CH;
-            x = c == 0 ? -2 : TX + c - 1;
-            y = e - c * CH - 2;
+        if (e < (2 * R + 1) * CH) {
+            const int c = e / CH;   // columns -R-1 .. -2, then TX .. TX + R
+            x = c < R ? c - C1 : TX + c - R;
+            y = e - c * CH - C1;
         } else {
-            const int e2 = e - 3 * CH, c = e2 >> 5;
-            y = c == 0 ? -2 : TY + c - 1;
+            const int e2 = e - (2 * R + 1) * CH, c = e2 >> 5;
+            y = c < R ? c - C1 : TY + c - R;
             x = (e2 & 31) - 1;
         }
-        exj[s] = (y + 2) * CW + (x + 2);
+        exj[s] = (y + C1) * CW + (x + C1);
         exX[s] = xidx(x, y);
         cell_q(x, y, eg[s], ePx[s], ePy[s]);
     }
@@ -410,7 +428,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     for (int r = 0; r < MR; r++) phbE[r] = phbN[r] = sumD[r] = T(0);
     const T gmc = p.ga1 * (T(1) - p.c2);    // gamma (1 - c2)
     T fn0Prev = T(0);                       // pending south difference of my first row
-    const int fbase = (fy0 + 2) * CW + (fx + 2);     // my first cell in the cell-quantity region
+    const int fbase = (fy0 + C1) * CW + (fx + C1);   // my first cell in the cell-quantity region
     const int xbase = xidx(fx, fy0);                 // ... in the state box
 
     // partial update of my cell r, direction k: X + beta (g - X) - gamma (1 - c2) Dbar
@@ -471,29 +489,29 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             if constexpr (T3A) part2_ref(k - 1, 0) -= gmc2 * d;
             sumD[0] += d;
         }
-        // S3b: face values of my MR cells from a (MR + 3) x 4 window of bar f^+_k
-        // (entries no tap uses are never loaded)
-        // (my own column of rows 0 .. MR - 1 is in registers)
-        T win[MR + 3][4];
+        // S3b: face values of my MR cells from an (MR + 2R + 1) x (2R + 2) window of
+        // bar f^+_k, rows -R .. MR + R, columns -R .. R + 1 (entries no tap uses are
+        // never loaded; my own column of rows 0 .. MR - 1 is in registers)
+        T win[MR + 2 * R + 1][2 * R + 2];
 #pragma unroll
-        for (int i = 0; i < MR + 3; i++)
+        for (int i = 0; i < MR + 2 * R + 1; i++)
 #pragma unroll
-            for (int a = 0; a < 4; a++)
-                win[i][a] = (a == 1 && i >= 1 && i <= MR) ? fo[i - 1] : F[fbase + (i - 1) * CW + (a - 1)];
+            for (int a = 0; a < 2 * R + 2; a++)
+                win[i][a] = (a == R && i >= R && i < R + MR) ? fo[i - R] : F[fbase + (i - R) * CW + (a - R)];
         T fe[MR], fn[MR];
 #pragma unroll
         for (int r = 0; r < MR; r++) {
             T se = T(0), sn = T(0);
 #pragma unroll
-            for (int b = 0; b < 3; b++)
+            for (int b = 0; b < 2 * R + 1; b++)
 #pragma unroll
-                for (int a = 0; a < 4; a++)
-                    if (tapE(FLUX, k, b - 1, a - 1)) se += cf.e[k][b][a] * win[r + b][a];
+                for (int a = 0; a < 2 * R + 2; a++)
+                    if (tapE(FLUX, k, b - R, a - R, R)) se += cf.e[k][b][a] * win[r + b][a];
 #pragma unroll
-            for (int b = 0; b < 4; b++)
+            for (int b = 0; b < 2 * R + 2; b++)
 #pragma unroll
-                for (int a = 0; a < 3; a++)
-                    if (tapN(FLUX, k, b - 1, a - 1)) sn += cf.n[k][b][a] * win[r + b][a];
+                for (int a = 0; a < 2 * R + 1; a++)
+                    if (tapN(FLUX, k, b - R, a - R, R)) sn += cf.n[k][b][a] * win[r + b][a];
             fe[r] = se;
             fn[r] = sn;
             phbE[r] += se;
@@ -673,20 +691,22 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     return true;
 }
 
-template <typename T, typename ST, int NW, int MR>
+template <typename T, typename ST, int NW, int MR, int R = 1>
 __device__ __forceinline__ uint64_t *fast_bar(unsigned char *smem) {
-    return reinterpret_cast<uint64_t *>(smem + FastTile<T, ST, NW, MR>::oBar);
+    return reinterpret_cast<uint64_t *>(smem + FastTile<T, ST, NW, MR, R>::oBar);
 }
 
 // One grid, one tile per CTA.
 template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR, int KIND = KIND_T2>
-__global__ void __launch_bounds__(NW * 32, (KIND == KIND_T3A ? FastTile<T, ST, NW, MR>::min_blocks_t3a
-                                                             : FastTile<T, ST, NW, MR>::min_blocks))
-step_fast_kernel(const __grid_constant__ StepParams<T> p, const __grid_constant__ FaceCoefs<T> cf,
+__global__ void __launch_bounds__(NW * 32,
+                                  (KIND == KIND_T3A ? FastTile<T, ST, NW, MR, (ORDER == 4 ? 2 : 1)>::min_blocks_t3a
+                                                    : FastTile<T, ST, NW, MR, (ORDER == 4 ? 2 : 1)>::min_blocks))
+step_fast_kernel(const __grid_constant__ StepParams<T> p,
+                 const __grid_constant__ FaceCoefs<T, (ORDER == 4 ? 2 : 1)> cf,
                  const __grid_constant__ FastExtra<T> fe_, const __grid_constant__ CUtensorMap tmX,
                  const __grid_constant__ CUtensorMap tmPo, const __grid_constant__ CUtensorMap tmPc) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bar = fast_bar<T, ST, NW, MR>(smem);
+    uint64_t *bar = fast_bar<T, ST, NW, MR, (ORDER == 4 ? 2 : 1)>(smem);
     if (threadIdx.x == 0) mbar_init(bar, 1);
     pdl_wait();   // the previous kernel's output (launched with programmatic serialization)
     double *mo = p.mass_partial ? p.mass_partial + blockIdx.y * p.tiles_x + blockIdx.x : nullptr;

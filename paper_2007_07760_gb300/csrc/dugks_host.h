@@ -18,41 +18,82 @@ namespace host {
 
 // ---- face stencils of the fast path ------------------------------------------
 // The face value bar f_k(x_b) is a fixed linear combination of bar f^+_k at the
-// cells around the face: the Taylor expansion of Eq. (26) (value + d.grad
-// + d d : H / 2 with the 9-point lattice-moment gradient and Hessian) about the
-// upwind cell, or the central form of Eq. (25). Weights at (a, b) of the
-// 3 x 3 block around the expansion cell:
-inline double G9x(int a, int b) { return a * (b == 0 ? 1.0 / 3.0 : 1.0 / 12.0); }
-inline double G9y(int a, int b) { return b * (a == 0 ? 1.0 / 3.0 : 1.0 / 12.0); }
-inline double H9(int i, int j, int a, int b) {   // i, j in {0: x, 1: y}
-    if (i != j) return (a != 0 && b != 0) ? 0.25 * a * b : 0.0;
+// cells around the face: the Taylor expansion of Eq. (26) about the upwind cell
+// (value + d.grad + d d : H / 2, + d d d : T / 6 at order 4), or the central form
+// of Eq. (25). Below: the weights at offset (a, b) from the expansion cell of the
+// stencils the generic kernel applies (orders 2-3: 9-point lattice moments;
+// order 4: the 21-point gradient, the Richardson Hessian (4 H_1 - H_2) / 3 and
+// second-order central third derivatives).
+inline double G9x(int a, int b) {
+    if (a < -1 || a > 1 || b < -1 || b > 1) return 0.0;
+    return a * (b == 0 ? 1.0 / 3.0 : 1.0 / 12.0);
+}
+inline double G9y(int a, int b) { return G9x(b, a); }
+inline double G21x(int a, int b) {   // weights 13/30, 2/15, -1/60 at (1, +-2), -1/60 at (2, 0), -1/30 at (2, +-1)
+    const int aa = a < 0 ? -a : a, bb = b < 0 ? -b : b, s = a < 0 ? -1 : 1;
+    if (aa == 0 || aa > 2 || bb > 2) return 0.0;
+    if (aa == 1) return s * (bb == 0 ? 13.0 / 30.0 : bb == 1 ? 2.0 / 15.0 : -1.0 / 60.0);
+    return s * (bb == 0 ? -1.0 / 60.0 : bb == 1 ? -1.0 / 30.0 : 0.0);
+}
+inline double G21y(int a, int b) { return G21x(b, a); }
+// 9-point lattice-moment Hessian with spacing S (points at S times the 3 x 3 block)
+inline double H9s(int i, int j, int a, int b, int S) {   // i, j in {0: x, 1: y}
+    if (a % S != 0 || b % S != 0) return 0.0;
+    a /= S;
+    b /= S;
+    if (a < -1 || a > 1 || b < -1 || b > 1) return 0.0;
+    const double inv = 1.0 / (S * S);
+    if (i != j) return (a != 0 && b != 0) ? 0.25 * a * b * inv : 0.0;
     const int along = i == 0 ? a : b, across = i == 0 ? b : a;
-    if (along == 0 && across == 0) return -4.0 / 3.0;
-    if (across == 0) return 2.0 / 3.0;
-    if (along == 0) return -1.0 / 3.0;
-    return 1.0 / 6.0;
+    if (along == 0 && across == 0) return -4.0 / 3.0 * inv;
+    if (across == 0) return 2.0 / 3.0 * inv;
+    if (along == 0) return -1.0 / 3.0 * inv;
+    return 1.0 / 6.0 * inv;
+}
+inline double Hp(int order, int i, int j, int a, int b) {
+    return order == 4 ? 4.0 / 3.0 * H9s(i, j, a, b, 1) - 1.0 / 3.0 * H9s(i, j, a, b, 2) : H9s(i, j, a, b, 1);
+}
+// third derivatives: txxx = (F(2,0) - F(-2,0)) / 2 - (F(1,0) - F(-1,0)); txxy = ((F(1,1) - F(1,-1))
+// + (F(-1,1) - F(-1,-1))) / 2 - (F(0,1) - F(0,-1)); tyyy, txyy by symmetry
+inline double Txxx(int a, int b) {
+    if (b != 0) return 0.0;
+    return a == 2 ? 0.5 : a == -2 ? -0.5 : a == 1 ? -1.0 : a == -1 ? 1.0 : 0.0;
+}
+inline double Txxy(int a, int b) {
+    if ((a == 1 || a == -1) && (b == 1 || b == -1)) return 0.5 * b;
+    if (a == 0 && (b == 1 || b == -1)) return -1.0 * b;
+    return 0.0;
 }
 inline double taylor_w(int order, double dx, double dy, int a, int b) {
     double w = (a == 0 && b == 0) ? 1.0 : 0.0;
-    w += dx * G9x(a, b) + dy * G9y(a, b);
+    if (order == 4) w += dx * G21x(a, b) + dy * G21y(a, b);
+    else w += dx * G9x(a, b) + dy * G9y(a, b);
     if (order >= 3)
-        w += 0.5 * dx * dx * H9(0, 0, a, b) + dx * dy * H9(0, 1, a, b) + 0.5 * dy * dy * H9(1, 1, a, b);
+        w += 0.5 * dx * dx * Hp(order, 0, 0, a, b) + dx * dy * Hp(order, 0, 1, a, b) +
+             0.5 * dy * dy * Hp(order, 1, 1, a, b);
+    if (order == 4)
+        w += (dx * dx * dx * Txxx(a, b) + 3.0 * dx * dx * dy * Txxy(a, b) + 3.0 * dx * dy * dy * Txxy(b, a) +
+              dy * dy * dy * Txxx(b, a)) / 6.0;
     return w;
 }
 
-template <typename T>
-inline FaceCoefs<T> make_face_coefs(int order, int flux, double h) {
-    double e[9][3][4] = {}, n[9][4][4] = {};
+// Face-stencil tables for stencil radius R (1: orders 2-3, 2: order 4).
+template <typename T, int R>
+inline FaceCoefs<T, R> make_face_coefs_r(int order, int flux, double h) {
+    constexpr int NE = 2 * R + 1, NA = 2 * R + 2;
+    double e[9][NE][NA] = {}, n[9][NA][NA] = {};
+    auto gx = [&](int a, int b) { return order == 4 ? G21x(a, b) : G9x(a, b); };
+    auto gy = [&](int a, int b) { return order == 4 ? G21y(a, b) : G9y(a, b); };
     for (int k = 0; k < 9; k++) {
         const int kx = ex(k), ky = ey(k);
-        // east face: taps (b, a) -> e[k][b + 1][a + 1], b in -1..1, a in -1..2
+        // east face: taps (b, a) -> e[k][b + R][a + R], b in -R..R, a in -R..R+1
         auto addE = [&](int cx, double wgt, double dx, double dy) {   // expansion about cell (cx, 0)
-            for (int b = -1; b <= 1; b++)
-                for (int a = -1; a <= 1; a++) e[k][b + 1][cx + a + 1] += wgt * taylor_w(order, dx, dy, a, b);
+            for (int b = -R; b <= R; b++)
+                for (int a = -R; a <= R; a++) e[k][b + R][cx + a + R] += wgt * taylor_w(order, dx, dy, a, b);
         };
         auto addN = [&](int cy, double wgt, double dx, double dy) {   // expansion about cell (0, cy)
-            for (int b = -1; b <= 1; b++)
-                for (int a = -1; a <= 1; a++) n[k][cy + b + 1][a + 1] += wgt * taylor_w(order, dx, dy, a, b);
+            for (int b = -R; b <= R; b++)
+                for (int a = -R; a <= R; a++) n[k][cy + b + R][a + R] += wgt * taylor_w(order, dx, dy, a, b);
         };
         if (flux == DUGKS_UPWIND) {
             if (kx > 0) addE(0, 1.0, 0.5 - h, -ky * h);
@@ -63,27 +104,32 @@ inline FaceCoefs<T> make_face_coefs(int order, int flux, double h) {
             else { addN(0, 0.5, -kx * h, 0.5); addN(1, 0.5, -kx * h, -0.5); }
         } else {
             // east: (F_c + F_E)/2 - h [xi_x (F_E - F_c) + xi_y (dF/dy(c) + dF/dy(E))/2]
-            e[k][1][1] += 0.5 + h * kx;
-            e[k][1][2] += 0.5 - h * kx;
-            n[k][1][1] += 0.5 + h * ky;
-            n[k][2][1] += 0.5 - h * ky;
-            for (int b = -1; b <= 1; b++)
-                for (int a = -1; a <= 1; a++) {
-                    e[k][b + 1][a + 1] += -0.5 * h * ky * G9y(a, b);
-                    e[k][b + 1][a + 2] += -0.5 * h * ky * G9y(a, b);
-                    n[k][b + 1][a + 1] += -0.5 * h * kx * G9x(a, b);
-                    n[k][b + 2][a + 1] += -0.5 * h * kx * G9x(a, b);
+            e[k][R][R] += 0.5 + h * kx;
+            e[k][R][R + 1] += 0.5 - h * kx;
+            n[k][R][R] += 0.5 + h * ky;
+            n[k][R + 1][R] += 0.5 - h * ky;
+            for (int b = -R; b <= R; b++)
+                for (int a = -R; a <= R; a++) {
+                    e[k][b + R][a + R] += -0.5 * h * ky * gy(a, b);
+                    e[k][b + R][a + R + 1] += -0.5 * h * ky * gy(a, b);
+                    n[k][b + R][a + R] += -0.5 * h * kx * gx(a, b);
+                    n[k][b + R + 1][a + R] += -0.5 * h * kx * gx(a, b);
                 }
         }
     }
-    FaceCoefs<T> cf;
+    FaceCoefs<T, R> cf;
     for (int k = 0; k < 9; k++) {
-        for (int b = 0; b < 3; b++)
-            for (int a = 0; a < 4; a++) cf.e[k][b][a] = (T)e[k][b][a];
-        for (int b = 0; b < 4; b++)
-            for (int a = 0; a < 4; a++) cf.n[k][b][a] = (T)n[k][b][a];
+        for (int b = 0; b < NE; b++)
+            for (int a = 0; a < NA; a++) cf.e[k][b][a] = (T)e[k][b][a];
+        for (int b = 0; b < NA; b++)
+            for (int a = 0; a < NA; a++) cf.n[k][b][a] = (T)n[k][b][a];
     }
     return cf;
+}
+
+template <typename T>
+inline FaceCoefs<T> make_face_coefs(int order, int flux, double h) {
+    return make_face_coefs_r<T, 1>(order, flux, h);
 }
 
 // ---- TMA tensor maps -----------------------------------------------------------

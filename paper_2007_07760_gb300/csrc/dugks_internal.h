@@ -34,7 +34,7 @@ struct Launch {
     static cudaError_t init(const StepParams<T> &p, const T *phi0, T frac_dt, int order, cudaStream_t s);
     static cudaError_t mass_partial(const StepParams<T> &p, cudaStream_t s);
     static cudaError_t phi(const StepParams<T> &p, T *out, cudaStream_t s);
-    static FastGeom fast_geom(int variant);
+    static FastGeom fast_geom(int variant, int order = 3);
     static cudaError_t batch_step(const BatchUniform<T> &u, const FaceCoefs<T> &cf, const BatchGrid<T> *grids,
                                   const int4 *items, int nitems, double *partials, int order, int flux, int variant,
                                   int ctas, cudaStream_t s);
@@ -42,6 +42,11 @@ struct Launch {
     static cudaError_t step_fast(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe, const CUtensorMap &tmX,
                                  const CUtensorMap &tmPo, const CUtensorMap &tmPc, int order, int flux,
                                  int variant, cudaStream_t s);
+    // order 4 (radius-2 stencils) on the TMA-staged path, tile 8 warps x 2 rows: the
+    // two-stage step (KIND_T2) or a kernel of the three-stage step (full storage only)
+    static cudaError_t step_fast4(const StepParams<T> &p, const FaceCoefs<T, 2> &cf, const FastExtra<T> &fe,
+                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc, int flux,
+                                  int kind, cudaStream_t s);
     // one kernel of the three-stage step (kind KIND_T3A or KIND_T3B) on the TMA-staged
     // path, tile 8 warps x 2 rows (full storage only: ST == T)
     static cudaError_t step_fast3(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,

@@ -2,21 +2,32 @@
 // dugks_inst_*.cu so the three precisions compile in parallel.
 #pragma once
 
+#include <atomic>
+
 #include "dugks_internal.h"
 
 namespace dugks {
+
+// Raises a kernel's dynamic shared-memory limit once per device (the attribute is
+// per function and device); `done` is the kernel's own bit set of devices.
+template <typename K>
+static cudaError_t smem_attr_once(K kern, int bytes, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_relaxed);
+    return e;
+}
 
 template <typename T, typename ST, int ORDER, int FLUX, int KIND>
 static cudaError_t launch_step_t(const StepParams<T> &p, cudaStream_t s) {
     using TL = Tile<T, ST, ORDER, FLUX, KIND, TILE_X, TILE_Y>;
     auto kern = step_kernel<T, ST, ORDER, FLUX, KIND, TILE_X, TILE_Y>;
-    static bool configured = false;   // per instantiation; the attribute is per function
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)TL::smem_bytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    if (cudaError_t e = smem_attr_once(kern, (int)TL::smem_bytes, configured); e != cudaSuccess) return e;
     dim3 grid((p.nx + TILE_X - 1) / TILE_X, (p.ny + TILE_Y - 1) / TILE_Y);
     kern<<<grid, STEP_THREADS, TL::smem_bytes, s>>>(p);
     return cudaGetLastError();
@@ -82,7 +93,11 @@ static FastGeom geom_t() {
 }
 
 template <typename T, typename ST>
-FastGeom Launch<T, ST>::fast_geom(int variant) {
+FastGeom Launch<T, ST>::fast_geom(int variant, int order) {
+    if (order == 4) {   // one tile shape for radius-2 stencils
+        using FT = FastTile<T, ST, 8, 2, 2>;
+        return FastGeom{FT::NT, FT::TX, FT::TY, FT::BW, FT::RH, FT::BWT};
+    }
     switch (variant) {
     case 1: return geom_t<T, ST, 16, 1>();
     case 2: return geom_t<T, ST, 8, 2>();
@@ -98,12 +113,8 @@ static cudaError_t launch_fast_t(const StepParams<T> &p, const FaceCoefs<T> &cf,
                                  const CUtensorMap &tmPo, const CUtensorMap &tmPc, cudaStream_t s) {
     using FT = FastTile<T, ST, NW, MR>;
     auto kern = step_fast_kernel<T, ST, ORDER, FLUX, NW, MR>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FT::smem_bytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    if (cudaError_t e = smem_attr_once(kern, (int)FT::smem_bytes, configured); e != cudaSuccess) return e;
     // programmatic dependent launch: scheduled while the previous kernel drains
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nx + FT::TX - 1) / FT::TX, (p.ny + FT::TY - 1) / FT::TY);
@@ -151,12 +162,8 @@ static cudaError_t launch_fast3_t(const StepParams<T> &p, const FaceCoefs<T> &cf
     using FT = FastTile<T, T, 8, 2>;
     constexpr size_t smem = KIND == KIND_T3A ? FT::smem_bytes_t3a : FT::smem_bytes;
     auto kern = step_fast_kernel<T, T, ORDER, FLUX, 8, 2, KIND>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    static std::atomic<uint64_t> configured{0};
+    if (cudaError_t e = smem_attr_once(kern, (int)smem, configured); e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((p.nx + FT::TX - 1) / FT::TX, (p.ny + FT::TY - 1) / FT::TY);
     cfg.blockDim = dim3(FT::NT);
@@ -187,6 +194,46 @@ cudaError_t Launch<T, ST>::step_fast3(const StepParams<T> &p, const FaceCoefs<T>
         DUGKS_T3(3, 1);
     }
 #undef DUGKS_T3
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, typename ST, int FLUX, int KIND>
+static cudaError_t launch_fast4_t(const StepParams<T> &p, const FaceCoefs<T, 2> &cf, const FastExtra<T> &fe,
+                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc,
+                                  cudaStream_t s) {
+    using FT = FastTile<T, ST, 8, 2, 2>;
+    constexpr size_t smem = KIND == KIND_T3A ? FT::smem_bytes_t3a : FT::smem_bytes;
+    auto kern = step_fast_kernel<T, ST, 4, FLUX, 8, 2, KIND>;
+    static std::atomic<uint64_t> configured{0};
+    if (cudaError_t e = smem_attr_once(kern, (int)smem, configured); e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nx + FT::TX - 1) / FT::TX, (p.ny + FT::TY - 1) / FT::TY);
+    cfg.blockDim = dim3(FT::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p, cf, fe, tmX, tmPo, tmPc);
+}
+
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::step_fast4(const StepParams<T> &p, const FaceCoefs<T, 2> &cf, const FastExtra<T> &fe,
+                                      const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc,
+                                      int flux, int kind, cudaStream_t s) {
+    if (kind == KIND_T2)
+        return flux == 0 ? launch_fast4_t<T, ST, 0, KIND_T2>(p, cf, fe, tmX, tmPo, tmPc, s)
+                         : launch_fast4_t<T, ST, 1, KIND_T2>(p, cf, fe, tmX, tmPo, tmPc, s);
+    if constexpr (!Store<T, ST>::deviation) {
+        if (kind == KIND_T3A)
+            return flux == 0 ? launch_fast4_t<T, ST, 0, KIND_T3A>(p, cf, fe, tmX, tmPo, tmPc, s)
+                             : launch_fast4_t<T, ST, 1, KIND_T3A>(p, cf, fe, tmX, tmPo, tmPc, s);
+        if (kind == KIND_T3B)
+            return flux == 0 ? launch_fast4_t<T, ST, 0, KIND_T3B>(p, cf, fe, tmX, tmPo, tmPc, s)
+                             : launch_fast4_t<T, ST, 1, KIND_T3B>(p, cf, fe, tmX, tmPo, tmPc, s);
+    }
     return cudaErrorInvalidValue;
 }
 

@@ -119,7 +119,7 @@ def test_batch_variants_match_single_grid(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("order,flux", [(2, 0), (3, 0), (3, 1)])
+@pytest.mark.parametrize("order,flux", [(2, 0), (3, 0), (3, 1), (4, 0), (4, 1)])
 def test_three_stage_fast_matches_oracle_and_generic(oracle, precision, order, flux):
     """The TMA-staged kernels of the three-stage scheme (two per step: tilde f at t'
     with the accumulator, then hat f) against the oracle and against the generic
@@ -145,3 +145,28 @@ def test_three_stage_fast_matches_oracle_and_generic(oracle, precision, order, f
         for v in out:
             assert np.abs(out[v][0] - ref).max() < FP32_TOL, v
         assert np.abs(out[2][0] - out[-1][0]).max() < 2e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16f"])
+@pytest.mark.parametrize("flux", [0, 1])
+def test_order4_fast_matches_oracle_and_generic(oracle, precision, flux):
+    """Order 4 (radius-2 stencils: 5-cell state halo, 3-cell cell-quantity halo,
+    5 x 6 face stencils) on the TMA-staged path against the oracle and the generic
+    kernel, ragged grid, rotation."""
+    nx, ny, steps = 77, 70, 60
+    phi0, vel = problem(nx, ny, "rotation", seed=60 + flux)
+    p = oracle.Params(nx, ny, W=4.0, M=0.02, cfl=0.8, order=4, flux=flux, stages=2, vel_kind="rotation", vel=vel)
+    ref = oracle.State(p, phi0).run(steps).phi()
+    out = {}
+    for v in (2, -1):
+        with N.Solver(nx, ny, phi0, vel_kind="rotation", vel=vel, W=4.0, M=0.02, cfl=0.8, order=4, flux=flux,
+                      stages=2, precision=precision) as s:
+            s.set_variant(v)
+            assert N.dugks_get_variant(s.ctx) == v
+            s.step(steps)
+            assert s.status() == 0
+            out[v] = s.phi()
+    tol = {"fp64": 1e-12, "fp32": FP32_TOL, "fp16f": 2e-3}[precision]
+    for v in out:
+        err = np.abs(out[v] - ref).max()
+        assert (err / np.abs(ref).max() if precision == "fp64" else err) < tol, (v, err)
