@@ -120,6 +120,15 @@ int dugks_mass_device(dugks_ctx *c, double *dev_out);
 /* Waits for the stream and returns the sticky status. */
 int dugks_status(dugks_ctx *c);
 
+/* Self-test of the device-side failure detection. Enqueues on the context's
+ * stream one CTA that waits, with the same bounded mbarrier wait that guards the
+ * step kernels' TMA copies, for 16 bytes that no copy ever delivers. After
+ * max_polls polls (1 .. 1048576) the wait gives up, the kernel records a timeout
+ * in the context's status word and returns: nothing faults, hangs or stays in
+ * flight, and the device stays usable. The next dugks_status (and every later
+ * call on this context) reports DUGKS_ETIMEOUT. DUGKS_EINVAL for a bad count. */
+int dugks_selftest_wait_timeout(dugks_ctx *c, uint32_t max_polls);
+
 /* Text of the last error; never NULL (empty when there was none). */
 const char *dugks_last_error(const dugks_ctx *c);
 

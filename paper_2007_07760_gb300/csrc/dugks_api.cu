@@ -679,6 +679,28 @@ int dugks_status(dugks_ctx *c) {
     return DUGKS_OK;
 }
 
+namespace {
+// one CTA waiting (bounded) on an mbarrier whose expected bytes never arrive
+__global__ void wait_timeout_kernel(uint32_t polls, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_expect_tx(&bar, 16);   // the arrival, with 16 bytes pending that nothing sends
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0, polls) && threadIdx.x == 0) atomicOr(status, 2);
+}
+}  // namespace
+
+int dugks_selftest_wait_timeout(dugks_ctx *c, uint32_t max_polls) {
+    if (!c || max_polls < 1 || max_polls > (1u << 20)) return DUGKS_EINVAL;
+    cudaSetDevice(c->dev);
+    wait_timeout_kernel<<<1, 32, 0, c->stream>>>(max_polls, c->dstatus);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "self-test kernel");
+    return DUGKS_OK;
+}
+
 int dugks_set_variant(dugks_ctx *c, int variant) {
     if (!c || variant < -1 || variant >= FAST_VARIANTS) return DUGKS_EINVAL;
     const bool fast_capable = (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) && encode_fn() != nullptr;

@@ -51,6 +51,7 @@ SIGNATURES = [
     ("dugks_mass", ctypes.c_int, [_VP, _DP]),
     ("dugks_mass_device", ctypes.c_int, [_VP, _VP]),
     ("dugks_status", ctypes.c_int, [_VP]),
+    ("dugks_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_uint32]),
     ("dugks_last_error", ctypes.c_char_p, [_VP]),
     ("dugks_step_index", _I64, [_VP]),
     ("dugks_set_variant", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -155,6 +156,11 @@ def dugks_mass_device(ctx, dev_ptr: int):
 
 def dugks_status(ctx) -> int:
     return lib().dugks_status(ctx)
+
+
+def dugks_selftest_wait_timeout(ctx, max_polls: int) -> int:
+    """Enqueues the bounded-wait self-test (see include/dugks.h); returns the code."""
+    return lib().dugks_selftest_wait_timeout(ctx, int(max_polls))
 
 
 def dugks_last_error(ctx) -> str:
