@@ -140,6 +140,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """The job's time is its slowest rank's: all-reduce MAX over the process group
+    (a CUDA tensor under NCCL, a host tensor under gloo); x itself without one."""
+    if dist is None or not dist.is_initialized():
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: the units all ranks processed
+    over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -314,13 +332,11 @@ def run_ours(args):
     K = args.steps
     res = time_single(solver, stream, args.warmup, K, dist, local)
     total_ms, avg_step_ms, clocks, mass = res["total_ms"], res["avg_step_ms"], res["clocks"], res["mass"]
+    total_ms = max_over_ranks(total_ms, dist)
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
 
-    value = prob.cells * K * world / (total_ms * 1e-3)
+    value = job_rate(prob.cells * K, world, total_ms * 1e-3)
     peak, peak_kind = measured_peak_hbm()
     achieved = BYTES_PER_CELL[args.precision] * prob.cells / (avg_step_ms * 1e-3) / 1e9
     sha = kernel_source_hash()
@@ -344,13 +360,9 @@ def run_ours(args):
         N.dugks_load_state(solver.ctx, host_state, idx)
         N.dugks_step(solver.ctx, 1)
         N.dugks_read_phi(solver.ctx, phi_host)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     tsize = 8 if args.precision == "fp64" else 4
-    e2e = {"value": prob.cells * Ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    e2e = {"value": job_rate(prob.cells * Ke, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": prob.cells * tsize, "steps": Ke,
            "path": "dugks_load_state(pinned host) + dugks_step + dugks_read_phi(host)"}
     solver.close()
@@ -446,16 +458,14 @@ def run_batch(args, dist, world, rank, local):
     K = args.steps
     r = measure_batch(count, args.precision, args.warmup, K, dist, local)
     total_ms, cells, desc = r["total_ms"], r["cells"], r["desc"]
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = cells * K * world / (total_ms * 1e-3)
+    total_ms = max_over_ranks(total_ms, dist)
+    e2e_s = max_over_ranks(r["e2e_s"], dist)
+    value = job_rate(cells * K, world, total_ms * 1e-3)
     peak, peak_kind = measured_peak_hbm()
     bpc = BYTES_PER_CELL[args.precision]
     achieved = bpc * cells / (total_ms / K * 1e-3) / 1e9
     tsize = 8 if args.precision == "fp64" else 4
-    e2e = {"value": cells * K * world / r["e2e_s"], "unit": UNIT,
+    e2e = {"value": job_rate(cells * K, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(cells * 8 / K), "d2h_bytes_per_step": int(cells * tsize / K),
            "path": "dugks_batch_add from host fields + K steps + dugks_batch_read_phi of every grid, amortised over K"}
     if rank == 0:
