@@ -432,12 +432,22 @@ int upload_plane(dugks_ctx *c, void *dst, const double *src) {
 
 namespace dugks {
 // Fixed-order sum of the per-tile partials (deterministic); flags NaN / Inf.
+// Thread t adds partials t, t + 256, ... in index order with 8 independent loads
+// in flight (one memory latency per 8 partials), then the fixed tree of block_sum.
+// One small CTA: it finds a free slot while the step kernel drains.
 __global__ void __launch_bounds__(256) mass_final_kernel(const double *partial, int n, double *out, int *status) {
     __shared__ double sred[32];
     pdl_trigger();
     pdl_wait();   // the partials of the step kernel ahead of it
+    constexpr int U = 8;
     double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+    for (int base = threadIdx.x; base < n; base += U * 256) {
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) v[u] = base + u * 256 < n ? partial[base + u * 256] : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; u++) s += v[u];
+    }
     s = block_sum(s, sred);
     if (threadIdx.x == 0) {
         *out = s;
