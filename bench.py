@@ -347,7 +347,7 @@ def run_ours(args):
     nbytes = N.dugks_state_bytes(solver.ctx)
     host_state = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
     idx = N.dugks_save_state(solver.ctx, host_state)
-    phi_host = np.empty((prob.ny, prob.nx))
+    phi_host = torch.empty((prob.ny, prob.nx), dtype=torch.float64, pin_memory=True).numpy()
     Ke = max(10, min(K, 500))
     for _ in range(3):
         N.dugks_load_state(solver.ctx, host_state, idx)

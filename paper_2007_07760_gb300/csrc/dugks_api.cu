@@ -530,7 +530,7 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     }
     for (int s = 0; s < c->nphi && ok; s++) ok = cudaMalloc(&c->phi[s], c->plane * c->tsize) == cudaSuccess;
     if (ok) ok = cudaMalloc(&c->phi0, c->plane * c->tsize) == cudaSuccess;
-    if (ok) ok = cudaMalloc(&c->tmp, (size_t)p->nx * p->ny * c->tsize) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->tmp, (size_t)p->nx * p->ny * sizeof(double)) == cudaSuccess;
     if (ok) ok = cudaMalloc(&c->dmass, sizeof(double)) == cudaSuccess;
     if (ok) ok = cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
     if (ok && c->fast) {
@@ -637,22 +637,23 @@ int dugks_read_phi_device(dugks_ctx *c, void *dev_out) {
 
 int dugks_read_phi(dugks_ctx *c, double *out_host) {
     if (!c || !out_host) return DUGKS_EINVAL;
-    int r = dugks_read_phi_device(c, c->tmp);
+    if (c->sticky != DUGKS_OK) return c->sticky;
+    cudaSetDevice(c->dev);
+    int r = ensure_init(c);
     if (r != DUGKS_OK) return r;
-    const size_t n = (size_t)c->p.nx * c->p.ny;
+    // phi widened to double on the device, then one copy into the caller's buffer
+    // (at full link speed when that buffer is pinned)
     cudaError_t e;
-    if (is_fp64(c)) {
-        e = cudaMemcpyAsync(out_host, c->tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "read phi");
-        return sync_ctx(c);
+    switch (c->p.precision) {
+    case DUGKS_FP64: e = Launch<double, double>::phi64(state_view<double, double>(c), static_cast<double *>(c->tmp), c->stream); break;
+    case DUGKS_FP32: e = Launch<float, float>::phi64(state_view<float, float>(c), static_cast<double *>(c->tmp), c->stream); break;
+    default: e = Launch<float, __half>::phi64(state_view<float, __half>(c), static_cast<double *>(c->tmp), c->stream); break;
     }
-    std::vector<float> tmp(n);
-    e = cudaMemcpyAsync(tmp.data(), c->tmp, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "phi kernel");
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    e = cudaMemcpyAsync(out_host, c->tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "read phi");
-    r = sync_ctx(c);
-    if (r != DUGKS_OK) return r;
-    for (size_t i = 0; i < n; i++) out_host[i] = tmp[i];
-    return DUGKS_OK;
+    return sync_ctx(c);
 }
 
 int dugks_mass_device(dugks_ctx *c, double *dev_out) {

@@ -509,7 +509,7 @@ int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host) {
     if (b->sticky != DUGKS_OK) return b->sticky;
     cudaSetDevice(b->dev);
     const Slot &s = b->slots[grid_id];
-    const size_t n = (size_t)s.nx * s.ny, bytes = n * b->tsize;
+    const size_t n = (size_t)s.nx * s.ny, bytes = n * sizeof(double);
     if (bytes > b->tmp_bytes) {
         cudaStreamSynchronize(b->stream);
         if (b->d_tmp) cudaFree(b->d_tmp);
@@ -521,22 +521,17 @@ int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host) {
         }
         b->tmp_bytes = bytes;
     }
+    // phi widened to double on the device, then one copy into the caller's buffer
     cudaError_t e;
+    double *d = static_cast<double *>(b->d_tmp);
     switch (b->p.precision) {
-    case DUGKS_FP64: e = Launch<double, double>::phi(slot_view<double, double>(b, s), static_cast<double *>(b->d_tmp), b->stream); break;
-    case DUGKS_FP32: e = Launch<float, float>::phi(slot_view<float, float>(b, s), static_cast<float *>(b->d_tmp), b->stream); break;
-    default: e = Launch<float, __half>::phi(slot_view<float, __half>(b, s), static_cast<float *>(b->d_tmp), b->stream); break;
+    case DUGKS_FP64: e = Launch<double, double>::phi64(slot_view<double, double>(b, s), d, b->stream); break;
+    case DUGKS_FP32: e = Launch<float, float>::phi64(slot_view<float, float>(b, s), d, b->stream); break;
+    default: e = Launch<float, __half>::phi64(slot_view<float, __half>(b, s), d, b->stream); break;
     }
     if (e != cudaSuccess) return bcuda(b, e, "phi kernel");
-    if (fp64(b)) {
-        e = cudaMemcpyAsync(out_host, b->d_tmp, bytes, cudaMemcpyDeviceToHost, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    } else {
-        std::vector<float> tmp(n);
-        e = cudaMemcpyAsync(tmp.data(), b->d_tmp, bytes, cudaMemcpyDeviceToHost, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        for (size_t i = 0; i < n && e == cudaSuccess; i++) out_host[i] = tmp[i];
-    }
+    e = cudaMemcpyAsync(out_host, d, bytes, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     return e == cudaSuccess ? b->sticky : bcuda(b, e, "read phi");
 }
 

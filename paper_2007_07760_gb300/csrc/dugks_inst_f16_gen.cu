@@ -7,4 +7,5 @@ template cudaError_t Launch<float,__half>::step(const StepParams<float> &, int, 
 template cudaError_t Launch<float,__half>::init(const StepParams<float> &, const float *, float, int, cudaStream_t);
 template cudaError_t Launch<float,__half>::mass_partial(const StepParams<float> &, cudaStream_t);
 template cudaError_t Launch<float,__half>::phi(const StepParams<float> &, float *, cudaStream_t);
+template cudaError_t Launch<float,__half>::phi64(const StepParams<float> &, double *, cudaStream_t);
 }  // namespace dugks

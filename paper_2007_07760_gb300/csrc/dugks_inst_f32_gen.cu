@@ -7,4 +7,5 @@ template cudaError_t Launch<float,float>::step(const StepParams<float> &, int, i
 template cudaError_t Launch<float,float>::init(const StepParams<float> &, const float *, float, int, cudaStream_t);
 template cudaError_t Launch<float,float>::mass_partial(const StepParams<float> &, cudaStream_t);
 template cudaError_t Launch<float,float>::phi(const StepParams<float> &, float *, cudaStream_t);
+template cudaError_t Launch<float,float>::phi64(const StepParams<float> &, double *, cudaStream_t);
 }  // namespace dugks

@@ -7,4 +7,5 @@ template cudaError_t Launch<double,double>::step(const StepParams<double> &, int
 template cudaError_t Launch<double,double>::init(const StepParams<double> &, const double *, double, int, cudaStream_t);
 template cudaError_t Launch<double,double>::mass_partial(const StepParams<double> &, cudaStream_t);
 template cudaError_t Launch<double,double>::phi(const StepParams<double> &, double *, cudaStream_t);
+template cudaError_t Launch<double,double>::phi64(const StepParams<double> &, double *, cudaStream_t);
 }  // namespace dugks

@@ -629,11 +629,11 @@ __global__ void __launch_bounds__(256) mass_partial_kernel(const StepParams<T> p
 }
 
 // phi of the state into a dense ny * nx array of T
-template <typename T, typename ST>
-__global__ void phi_kernel(const StepParams<T> p, T *out) {
+template <typename T, typename ST, typename O = T>
+__global__ void phi_kernel(const StepParams<T> p, O *out) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
     if (gx >= p.nx || gy >= p.ny) return;
-    out[(size_t)gy * p.nx + gx] = cell_phi<T, ST>(p, gidx(p, gx, gy));
+    out[(size_t)gy * p.nx + gx] = (O)cell_phi<T, ST>(p, gidx(p, gx, gy));
 }
 
 }  // namespace dugks

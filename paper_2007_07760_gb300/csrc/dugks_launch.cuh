@@ -244,6 +244,13 @@ cudaError_t Launch<T, ST>::phi(const StepParams<T> &p, T *out, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename T, typename ST>
+cudaError_t Launch<T, ST>::phi64(const StepParams<T> &p, double *out, cudaStream_t s) {
+    dim3 block(128), grid((p.nx + 127) / 128, p.ny);
+    phi_kernel<T, ST, double><<<grid, block, 0, s>>>(p, out);
+    return cudaGetLastError();
+}
+
 
 template <typename T, typename ST, int ORDER, int FLUX, int NW, int MR>
 static cudaError_t launch_batch_t(const BatchUniform<T> &u, const FaceCoefs<T> &cf, const BatchGrid<T> *grids,
