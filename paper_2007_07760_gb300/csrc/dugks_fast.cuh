@@ -1,22 +1,25 @@
-// dugks_fast.cuh -- the two-stage DUGKS step for stencil orders 2 and 3, staged
-// by TMA (sm_103a).
+// dugks_fast.cuh -- the DUGKS step staged by TMA (sm_103a): the two-stage step
+// and the two kernels of the three-stage step, stencil orders 2 to 4.
 //
 // Same arithmetic as step_kernel (dugks_kernels.cuh), organised for throughput:
-//  * the tile's 9 distribution planes plus a 3-cell halo arrive in shared
-//    memory as ONE 3D TMA box (the ghost border of the plane layout makes every
-//    halo a plain rectangle), the older phi plane as a 2D box; one mbarrier;
-//  * the loop over the 9 velocities is outermost (and not unrolled, to keep the
-//    kernel small enough for the instruction cache): per direction k,
-//    bar f^+_k on the tile + 2 cells, then bar f_k at the east and north faces
-//    of every face-owner cell as fixed 12-tap linear stencils of bar f^+_k
-//    (coefficients depend only on k and h: computed on the host);
+//  * the tile's 9 distribution planes plus a halo of 1 + 2R cells (stencil radius
+//    R = 1 for orders 2-3, 2 for order 4) arrive in shared memory as ONE 3D TMA
+//    box (the ghost border of the plane layout makes every halo a plain
+//    rectangle), the older phi plane as a 2D box; one mbarrier, bounded wait;
+//  * the loop over the 9 velocities is outermost and unrolled (lattice constants,
+//    stencil coefficients and the stencils' structural zeros are compile-time per
+//    direction): per direction k, bar f^+_k on the tile + R + 1 cells, then bar
+//    f_k at the east and north faces of every face-owner cell as fixed linear
+//    stencils of bar f^+_k ((2R+1) x (2R+2) taps; coefficients depend only on k
+//    and h: computed on the host);
 //  * the flux of Eq. (21) is split as
 //      L_k = -[(1 - c2) Dbar_k + c2 w_k Phi_k + c3 w_k Psi_k]
 //    with Dbar_k the face-difference of bar f_k, Phi_k that of
 //    f^eq_b / w_k = phi_b + 3 xi_k.(phi_b u_b) and Psi_k that of xi_k.V_b.
 //    During the direction loop each cell's X_k + beta (g_k - X_k) + gamma L_k
 //    minus its phi_b part is written over X_k in the TMA buffer (dead by then);
-//    once phi_b is known, a second loop adds the phi_b part and stores.
+//    once phi_b is known, a second loop adds the phi_b part (in closed form over
+//    k) and stores.
 // Thread layout: a warp owns 32 consecutive face-owner columns (lane l is column
 // l - 1) and MR consecutive rows; the CTA's face owners are 32 x (NW * MR), its
 // cells TX = 31 by TY = NW * MR - 1.

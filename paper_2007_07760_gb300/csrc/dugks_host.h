@@ -21,7 +21,7 @@ namespace host {
 // cells around the face: the Taylor expansion of Eq. (26) about the upwind cell
 // (value + d.grad + d d : H / 2, + d d d : T / 6 at order 4), or the central form
 // of Eq. (25). Below: the weights at offset (a, b) from the expansion cell of the
-// stencils the generic kernel applies (orders 2-3: 9-point lattice moments;
+// stencils the generic kernel applies (orders 2 and 3: 9-point lattice moments;
 // order 4: the 21-point gradient, the Richardson Hessian (4 H_1 - H_2) / 3 and
 // second-order central third derivatives).
 inline double G9x(int a, int b) {
