@@ -359,12 +359,15 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             nyv = gyp * inv;
         }
         const T theta = p.theta_c * (ph - p.phiA) * (ph - p.phiB);  // Eq. (4)
-        T u, v;
-        vel(x, y, 0, p.t, fe_.vc_t, u, v);
+        // the velocity at the cell centre at both time levels: the vortex's spatial
+        // part once, scaled by its reversal factor; the other kinds do not depend on t
+        const bool vortex = p.vel_kind == VEL_VORTEX;
+        T u0, v0;
+        vel(x, y, 0, p.t, vortex ? T(1) : fe_.vc_t, u0, v0);
+        const T u = vortex ? u0 * fe_.vc_t : u0, v = vortex ? v0 * fe_.vc_t : v0;
         T Dx = T(0), Dy = T(0);
         if (p.useD) {  // d(phi u)/dt, backward difference
-            T uo, vo;
-            vel(x, y, 0, p.t_old, fe_.vc_told, uo, vo);
+            const T uo = vortex ? u0 * fe_.vc_told : u0, vo = vortex ? v0 * fe_.vc_told : v0;
             const T po = sPo[(y + H) * BWT + (x + H + oxt)];
             Dx = (ph * u - po * uo) * p.inv_dtD;
             Dy = (ph * v - po * vo) * p.inv_dtD;
