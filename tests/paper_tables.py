@@ -1,0 +1,26 @@
+"""The paper's printed diagonal-translation errors (tests/golden/translation_e_phi.json)
+and the error measure they use; shared by the oracle and GPU table tests."""
+import json
+import os
+
+import numpy as np
+
+from paper_2007_07760_gb300 import workloads as WL
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "translation_e_phi.json")
+SCHEMES = {"T2S2CD": (2, 1, 2), "T2S3": (3, 0, 2), "T3S3": (3, 0, 3)}   # order, flux, stages
+
+
+def paper_value(scheme: str, cfl: float, n: int) -> float:
+    t = json.load(open(GOLDEN))
+    return t["E_phi"][scheme][str(cfl)][t["N"].index(n)]
+
+
+def problem(scheme: str, cfl: float, n: int):
+    order, flux, stages = SCHEMES[scheme]
+    return WL.translation(n, order, flux, stages, cfl)
+
+
+def e_phi(phi: np.ndarray, phi0: np.ndarray) -> float:
+    """L2-norm error of phi against the initial field (the measure of Sec. III)."""
+    return float(np.sqrt(((phi - phi0) ** 2).sum() / (phi0 ** 2).sum()))
