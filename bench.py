@@ -40,7 +40,7 @@ from paper_2007_07760_gb300 import workloads as WL  # noqa: E402
 
 METRIC = "D2Q9 cell-updates/s"
 UNIT = "cell-updates/s"
-BYTES_PER_CELL = {"fp64": 160, "fp32": 80, "fp16f": 48}   # two-stage, with d(phi u)/dt
+BYTES_PER_CELL = {"fp64": 160, "fp32": 84, "fp16f": 48}   # two-stage, with d(phi u)/dt
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes) of one step

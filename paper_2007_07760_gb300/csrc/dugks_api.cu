@@ -153,11 +153,11 @@ int run_init(dugks_ctx *c) {
     StepParams<T> q = base_params<T>(c);
     q.t = (T)0;
     const double frac = c->p.stages == 2 ? 0.5 : 0.25;
-    if (Store<T, ST>::deviation) {
+    if (Store<T, ST>::phi_plane) {
         c->pr[0] = 0; c->pr[1] = 1; c->pr[2] = 2;
     }
     q.out1 = c->p.stages == 3 ? c->X[0] : c->X[c->cur];
-    // deviation storage: phi of the state; otherwise phi0 as the previous level
+    // a phi plane: phi of the state; otherwise phi0 as the previous level
     q.phi_out = static_cast<T *>(c->phi[c->pr[0]]);
     cudaError_t e = Launch<T, ST>::init(q, static_cast<const T *>(c->phi0), (T)(frac * c->p.cfl), c->p.order, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
@@ -170,7 +170,7 @@ int ensure_init(dugks_ctx *c) {
     if (c->initialized) return DUGKS_OK;
     switch (c->p.precision) {
     case DUGKS_FP64: return run_init<double, double>(c);
-    case DUGKS_FP32: return run_init<float, float>(c);
+    case DUGKS_FP32: return c->p.stages == 3 ? run_init<float, float>(c) : run_init<float, PhiF32>(c);
     default: return run_init<float, __half>(c);
     }
 }
@@ -189,9 +189,9 @@ FastExtra<T> vortex_factors(const dugks_ctx *c, double t, double t_old, double t
     return fx;
 }
 
-// One two-stage step. Full storage: X[cur] -> X[1-cur]; phi[pr0] holds
-// phi^{n-1}, phi[pr1] receives phi^n. Deviation storage: phi[pr0] = phi^n
-// (of X), phi[pr1] = phi^{n-1}, phi[pr2] receives phi^{n+1}.
+// One two-stage step, X[cur] -> X[1-cur]. phi as a sum of X (FP64): phi[pr0]
+// holds phi^{n-1}, phi[pr1] receives phi^n. phi as a plane of its own (FP32,
+// FP16F): phi[pr0] = phi^n (of X), phi[pr1] = phi^{n-1}, phi[pr2] receives phi^{n+1}.
 template <typename T, typename ST>
 int step_t2(dugks_ctx *c) {
     StepParams<T> q = base_params<T>(c);
@@ -208,13 +208,14 @@ int step_t2(dugks_ctx *c) {
     q.t = (T)t;
     q.t_old = (T)(t - dt);
     q.t_face = (T)(t + h);
+    q.seed = (uint32_t)c->step;
     q.useD = (c->p.dtphiu && c->step > 0) ? 1 : 0;
     q.inv_dtD = (T)(1.0 / dt);
     q.X = c->X[c->cur];
     q.out1 = c->X[1 - c->cur];
     q.mass_partial = c->partial;
     int iPc = 0, iPo, iOut;
-    if (Store<T, ST>::deviation) {
+    if (Store<T, ST>::phi_plane) {
         iPc = c->pr[0]; iPo = c->pr[1]; iOut = c->pr[2];
         q.phi_cur = static_cast<const T *>(c->phi[iPc]);
     } else {
@@ -254,7 +255,7 @@ int step_t2(dugks_ctx *c) {
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
     c->cur = 1 - c->cur;
-    if (Store<T, ST>::deviation) {
+    if (Store<T, ST>::phi_plane) {
         const int a0 = c->pr[0], a1 = c->pr[1], a2 = c->pr[2];
         c->pr[0] = a2; c->pr[1] = a0; c->pr[2] = a1;
     } else {
@@ -360,7 +361,7 @@ int step_once(dugks_ctx *c) {
     } else {
         switch (c->p.precision) {
         case DUGKS_FP64: r = step_t2<double, double>(c); break;
-        case DUGKS_FP32: r = step_t2<float, float>(c); break;
+        case DUGKS_FP32: r = step_t2<float, PhiF32>(c); break;
         default: r = step_t2<float, __half>(c); break;
         }
     }
@@ -375,7 +376,7 @@ template <typename T, typename ST>
 StepParams<T> state_view(const dugks_ctx *c) {
     StepParams<T> q = base_params<T>(c);
     q.X = c->p.stages == 3 ? c->X[0] : c->X[c->cur];
-    if (Store<T, ST>::deviation) q.phi_cur = static_cast<const T *>(c->phi[c->pr[0]]);
+    if (Store<T, ST>::phi_plane) q.phi_cur = static_cast<const T *>(c->phi[c->pr[0]]);
     q.mass_partial = c->partial;
     return q;
 }
@@ -385,7 +386,10 @@ int enqueue_mass(dugks_ctx *c, double *dev_out) {
     if (!c->mass_valid) {
         switch (c->p.precision) {
         case DUGKS_FP64: e = Launch<double, double>::mass_partial(state_view<double, double>(c), c->stream); break;
-        case DUGKS_FP32: e = Launch<float, float>::mass_partial(state_view<float, float>(c), c->stream); break;
+        case DUGKS_FP32:
+            e = c->p.stages == 3 ? Launch<float, float>::mass_partial(state_view<float, float>(c), c->stream)
+                                 : Launch<float, PhiF32>::mass_partial(state_view<float, PhiF32>(c), c->stream);
+            break;
         default: e = Launch<float, __half>::mass_partial(state_view<float, __half>(c), c->stream); break;
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "mass partial kernel");
@@ -400,7 +404,11 @@ int enqueue_phi(dugks_ctx *c, void *dev_out) {
     cudaError_t e;
     switch (c->p.precision) {
     case DUGKS_FP64: e = Launch<double, double>::phi(state_view<double, double>(c), static_cast<double *>(dev_out), c->stream); break;
-    case DUGKS_FP32: e = Launch<float, float>::phi(state_view<float, float>(c), static_cast<float *>(dev_out), c->stream); break;
+    case DUGKS_FP32:
+        e = c->p.stages == 3
+                ? Launch<float, float>::phi(state_view<float, float>(c), static_cast<float *>(dev_out), c->stream)
+                : Launch<float, PhiF32>::phi(state_view<float, PhiF32>(c), static_cast<float *>(dev_out), c->stream);
+        break;
     default: e = Launch<float, __half>::phi(state_view<float, __half>(c), static_cast<float *>(dev_out), c->stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "phi kernel");
@@ -506,7 +514,8 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     c->pitch = (p->nx + 2 * GHOST + 31) / 32 * 32;
     c->plane = (size_t)(p->ny + 2 * GHOST) * c->pitch;
     c->nsets = p->stages == 3 ? 3 : 2;
-    c->nphi = p->precision == DUGKS_FP16F ? 3 : 2;
+    // two-stage FP32 and FP16F keep phi as a plane of its own: three rotating roles
+    c->nphi = (p->precision == DUGKS_FP16F || (p->precision == DUGKS_FP32 && p->stages == 2)) ? 3 : 2;
     // the TMA-staged kernels serve every order and both schemes (three-stage: full
     // storage; order 4 and the three-stage scheme: one tile shape, 8 x 2)
     c->fast = (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
@@ -535,7 +544,7 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     if (ok) ok = cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
     if (ok && c->fast) {
         bool enc = p->precision == DUGKS_FP64 ? setup_fast<double, double>(c)
-                   : p->precision == DUGKS_FP32 ? setup_fast<float, float>(c)
+                   : p->precision == DUGKS_FP32 ? (p->stages == 3 ? setup_fast<float, float>(c) : setup_fast<float, PhiF32>(c))
                                                 : setup_fast<float, __half>(c);
         if (!enc) {   // use the generic CUDA kernel instead
             c->fast = false;
@@ -646,7 +655,11 @@ int dugks_read_phi(dugks_ctx *c, double *out_host) {
     cudaError_t e;
     switch (c->p.precision) {
     case DUGKS_FP64: e = Launch<double, double>::phi64(state_view<double, double>(c), static_cast<double *>(c->tmp), c->stream); break;
-    case DUGKS_FP32: e = Launch<float, float>::phi64(state_view<float, float>(c), static_cast<double *>(c->tmp), c->stream); break;
+    case DUGKS_FP32:
+        e = c->p.stages == 3
+                ? Launch<float, float>::phi64(state_view<float, float>(c), static_cast<double *>(c->tmp), c->stream)
+                : Launch<float, PhiF32>::phi64(state_view<float, PhiF32>(c), static_cast<double *>(c->tmp), c->stream);
+        break;
     default: e = Launch<float, __half>::phi64(state_view<float, __half>(c), static_cast<double *>(c->tmp), c->stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "phi kernel");
@@ -729,7 +742,7 @@ int dugks_set_variant(dugks_ctx *c, int variant) {
         c->fast = true;
         c->variant = variant;
         const bool ok = c->p.precision == DUGKS_FP64 ? setup_fast<double, double>(c)
-                        : c->p.precision == DUGKS_FP32 ? setup_fast<float, float>(c)
+                        : c->p.precision == DUGKS_FP32 ? (c->p.stages == 3 ? setup_fast<float, float>(c) : setup_fast<float, PhiF32>(c))
                                                        : setup_fast<float, __half>(c);
         if (!ok) return fail(c, DUGKS_ECUDA, "tensor map encoding failed");
     }
@@ -754,7 +767,8 @@ const char *dugks_last_error(const dugks_ctx *c) { return c ? c->err.c_str() : "
 
 int64_t dugks_step_index(const dugks_ctx *c) { return c ? c->step : -1; }
 
-static int saved_phi_planes(const dugks_ctx *c) { return c->p.precision == DUGKS_FP16F ? 2 : 1; }
+// phi of the state and of the previous level where phi is a plane of its own
+static int saved_phi_planes(const dugks_ctx *c) { return c->nphi == 3 ? 2 : 1; }
 
 size_t dugks_state_bytes(const dugks_ctx *c) {
     if (!c) return 0;

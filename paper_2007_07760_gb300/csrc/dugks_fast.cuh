@@ -193,14 +193,14 @@ struct FastTile {
     static constexpr int AT = 16 / (int)sizeof(T);          // ... of the phi planes
     static constexpr int BW = (RW + AS - 1 + AS - 1) / AS * AS;   // state box width
     static constexpr int BWT = (RW + AT - 1 + AT - 1) / AT * AT;  // phi box width
-    static constexpr bool DEV = Store<T, ST>::deviation;
+    static constexpr bool DEV = Store<T, ST>::deviation, PHIP = Store<T, ST>::phi_plane;
     // shared-memory carve-up (byte offsets, 128-B aligned TMA destinations first)
     static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
     static constexpr size_t oX = 0;
     static constexpr size_t oPo = al(oX + sizeof(ST) * 9 * BW * RH);
     static constexpr size_t oPc = al(oPo + sizeof(T) * BWT * RH);
-    static constexpr size_t oPhi = al(oPc + (DEV ? sizeof(T) * BWT * RH : 0));
-    static constexpr size_t oPart = al(oPhi + (DEV ? 0 : sizeof(T) * RW * RH));
+    static constexpr size_t oPhi = al(oPc + (PHIP ? sizeof(T) * BWT * RH : 0));
+    static constexpr size_t oPart = al(oPhi + (PHIP ? 0 : sizeof(T) * RW * RH));
     static constexpr size_t oV = al(oPart + (DEV ? sizeof(T) * 9 * 32 * (TY + 1) : 0));
     static constexpr size_t oF = al(oV + sizeof(T) * 2 * NC);
     static constexpr size_t oNB = al(oF + sizeof(T) * 2 * NC);
@@ -210,7 +210,7 @@ struct FastTile {
     static constexpr size_t oBar = oRed + sizeof(double) * 32;
     static constexpr size_t smem_bytes = oBar + 16;
     static constexpr uint32_t tx_bytes =
-        (uint32_t)(sizeof(ST) * 9 * BW * RH + sizeof(T) * BWT * RH * (DEV ? 2 : 1));
+        (uint32_t)(sizeof(ST) * 9 * BW * RH + sizeof(T) * BWT * RH * (PHIP ? 2 : 1));
     // resident CTAs per SM that shared memory allows (228 KiB per SM, 1 KiB reserved
     // per CTA) and threads allow, without asking for fewer than 64 registers per thread:
     // the register target of the launch bounds, so that registers never cut occupancy
@@ -241,14 +241,14 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     constexpr int TX = FT::TX, TY = FT::TY, RW = FT::RW, CW = FT::CW, CH = FT::CH, NC = FT::NC;
     constexpr int NT = FT::NT, BW = FT::BW, BWT = FT::BWT, RH = FT::RH, NE = FT::NE, NXS = FT::NXS;
     constexpr int H = FT::H, C1 = FT::C1;
-    constexpr bool DEV = FT::DEV;
+    constexpr bool DEV = FT::DEV, PHIP = FT::PHIP;
     static_assert(ORDER >= 2 && ORDER <= 4, "stencil orders 2 to 4");
     // KIND_T2: the two-stage step. KIND_T3A / KIND_T3B: the two kernels of the
     // three-stage step (Sec. II.B.2), full storage only:
     //   T3A  out1 = X + be1 (g - X) + ga1 L (tilde f at t'), out2 = X + be2 (g - X) + ga2 L
     //        (the accumulator, in T), phi_out = phi of X;
     //   T3B  out1 = acc + be1 (g - X) + ga1 L (hat f at t_n + dt; al1 = -be1), mass partial.
-    static_assert(KIND == KIND_T2 || !DEV, "the three-stage scheme keeps full values");
+    static_assert(KIND == KIND_T2 ? Store<T, ST>::t2 : Store<T, ST>::t3, "scheme not served by this storage");
     constexpr bool T3A = KIND == KIND_T3A, T3B = KIND == KIND_T3B;
 
     ST *sX = reinterpret_cast<ST *>(smem + FT::oX);
@@ -280,7 +280,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         mbar_expect_tx(bar, FT::tx_bytes);
         tma_load_3d(sX, tmX, xs, ys, 0, bar);
         tma_load_2d(sPo, tmPo, xst, ys, bar);
-        if constexpr (DEV) tma_load_2d(sPc, tmPc, xst, ys, bar);
+        if constexpr (PHIP) tma_load_2d(sPc, tmPc, xst, ys, bar);
     }
     // while the copy is in flight: velocity tables
     // single vortex u = -U A(x) B(y) c(t), v = U A(y) B(x) c(t), with
@@ -318,7 +318,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     // accessors (relative cell coordinates x, y of the tile)
     auto xidx = [&](int x, int y) { return (y + H) * BW + (x + H + ox); };   // + k * RH * BW
     auto PHI = [&](int x, int y) -> T {
-        if constexpr (DEV) return sPc[(y + H) * BWT + (x + H + oxt)];
+        if constexpr (PHIP) return sPc[(y + H) * BWT + (x + H + oxt)];
         else return sPhi[(y + H) * RW + (x + H)];
     };
     // velocity of a cell centre (where = 0), east face (1) or north face (2)
@@ -344,7 +344,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         ph = PHI(x, y);
         T gxp, gyp;
         if constexpr (ORDER == 4) {   // the order's own gradient (Sec. II.B.1)
-            if constexpr (DEV) grad21(sPc + (y + H) * BWT + (x + H + oxt), BWT, gxp, gyp);
+            if constexpr (PHIP) grad21(sPc + (y + H) * BWT + (x + H + oxt), BWT, gxp, gyp);
             else grad21(sPhi + (y + H) * RW + (x + H), RW, gxp, gyp);
         } else {
             const T ne = PHI(x + 1, y + 1), nw = PHI(x - 1, y + 1), se = PHI(x + 1, y - 1), sw = PHI(x - 1, y - 1);
@@ -381,7 +381,8 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     };
 
     // ---- S1: phi = sum_k X_k on the state region (Eq. (30)) ------------------
-    if constexpr (!DEV) {
+    // (a phi plane already holds it)
+    if constexpr (!PHIP) {
         for (int y = warp - H; y < RH - H; y += NW)
             for (int x = lane - H; x < RW - H; x += 32) {
                 const int xi = xidx(x, y);
@@ -652,7 +653,11 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         const T B2 = T(3) * gc2 * (dE[2] + dN[1]) + gc3 * (dVEy + dVNx);
         const T B3 = T(3) * gc2 * dN[2] + gc3 * dVNy;
         // new phi = phi + gamma sum_k L_k (sum_k w_k xi_k = 0, sum_k w_k xi_a xi_b = delta_ab / 3)
-        const T phn = cg[r] - gmc * sumD[r] - (B1 + B3) * T(1.0 / 3.0);
+        // (a phi plane: the flux sum added with unbiased stochastic rounding)
+        const T dphi = -gmc * sumD[r] - (B1 + B3) * T(1.0 / 3.0);
+        T phn;
+        if constexpr (PHIP) phn = add_sr(cg[r], dphi, sr_bits(p, gx, gy));
+        else phn = cg[r] + dphi;
         const bool edge = gx < GHOST || gx >= nx - GHOST || gy < GHOST || gy >= ny - GHOST;
         const size_t g = gidx(p, gx, gy);
         T o[9];
@@ -682,11 +687,14 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             if (edge)
                 put_ghosts9(p, Oq, gx, gy, phn, qv[0], qv[1], qv[2], qv[3], qv[4], qv[5], qv[6], qv[7], qv[8]);
         } else {
+            // a phi plane receives the new phi; otherwise phi_out is phi of X (the
+            // older level of the next step's d(phi u)/dt)
+            const T pho = PHIP ? phn : cg[r];
             T *O = static_cast<T *>(p.out1);
 #pragma unroll
             for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
-            p.phi_out[g] = cg[r];
-            if (edge) put_ghosts9(p, O, gx, gy, cg[r], o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
+            p.phi_out[g] = pho;
+            if (edge) put_ghosts9(p, O, gx, gy, pho, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
         }
         msum += (double)phn;
     }
@@ -758,7 +766,7 @@ __global__ void __launch_bounds__(NW * 32, (FastTile<T, ST, NW, MR>::min_blocks)
 batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_constant__ FaceCoefs<T> cf,
                   const BatchGrid<T> *__restrict__ grids, const int4 *__restrict__ items, int nitems,
                   double *__restrict__ partials) {
-    constexpr bool DEV = Store<T, ST>::deviation;
+    constexpr bool PHIP = Store<T, ST>::phi_plane;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = fast_bar<T, ST, NW, MR>(smem);
     if (threadIdx.x == 0) mbar_init(bar, 1);
@@ -797,6 +805,7 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
         p.phiB = u.phiB;
         p.inv_dtD = u.inv_dt;
         p.useD = (u.dtphiu && step > 0) ? 1 : 0;
+        p.seed = (uint32_t)step;
         p.vel_kind = G->vel_kind;
         p.vp0 = (T)G->vp[0];
         p.vp1 = (T)G->vp[1];
@@ -819,7 +828,7 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
         p.X = G->X[cur];
         p.out1 = G->X[1 - cur];
         int iPc = 0, iPo, iOut;
-        if constexpr (DEV) {   // roles rotate with period 3 (see the context API)
+        if constexpr (PHIP) {   // roles rotate with period 3 (see the context API)
             iPc = (3 - (int)(step % 3)) % 3;
             iPo = (iPc + 1) % 3;
             iOut = (iPc + 2) % 3;
@@ -835,7 +844,7 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
             // tensor maps written to global memory by the host: order them for the TMA unit
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmX[cur]) : "memory");
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmPhi[iPo]) : "memory");
-            if constexpr (DEV)
+            if constexpr (PHIP)
                 asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmPhi[iPc]) : "memory");
         }
         if (!fast_tile<T, ST, ORDER, FLUX, NW, MR>(p, cf, fe, &G->tmX[cur], &G->tmPhi[iPo], &G->tmPhi[iPc], w.y, w.z,

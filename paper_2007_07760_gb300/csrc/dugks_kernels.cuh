@@ -43,17 +43,36 @@ __host__ __device__ __forceinline__ constexpr T wq(int k) {
 enum Kind { KIND_T2 = 0, KIND_T3A = 1, KIND_T3B = 2 };
 enum Vel { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_FIELD = 3 };
 
-// Storage of the distribution: full values of type T, or (FP16F) half-precision
-// scaled deviations q_k = (f_k - w_k phi) * s / w_k with phi kept as a T plane.
+// FP32 full values of the two-stage scheme whose phi is its own plane (the
+// storage tag of that layout; converts to float on reads)
+struct PhiF32 {
+    float v;
+    __host__ __device__ operator float() const { return v; }
+};
+
+// Storage of the distribution and of phi:
+//  * Store<T, T>: full values of type T; phi of a state is sum_k X_k
+//    (FP64, both schemes; FP32 three-stage)
+//  * Store<float, PhiF32>: full FP32 values plus phi as an FP32 plane of its own,
+//    updated by phi + sum of the face fluxes with unbiased stochastic rounding
+//    (FP32 two-stage); sum_k X_k equals that phi up to rounding
+//  * Store<float, __half>: half-precision scaled deviations
+//    q_k = (f_k - w_k phi) * s / w_k, phi likewise its own plane (FP16F, two-stage)
+// phi_plane: phi is read from and written to its plane (roles rotate over three
+// planes) rather than summed; t2 / t3: the schemes that storage serves.
 template <typename T, typename ST>
 struct Store;
 template <typename T>
 struct Store<T, T> {
-    static constexpr bool deviation = false;
+    static constexpr bool deviation = false, phi_plane = false, t2 = sizeof(T) == 8, t3 = true;
+};
+template <>
+struct Store<float, PhiF32> {
+    static constexpr bool deviation = false, phi_plane = true, t2 = true, t3 = false;
 };
 template <>
 struct Store<float, __half> {
-    static constexpr bool deviation = true;
+    static constexpr bool deviation = true, phi_plane = true, t2 = true, t3 = false;
 };
 
 // Storage layout of every plane: (ny + 2 GHOST) rows of `pitch` elements; cell
@@ -90,6 +109,7 @@ struct StepParams {
     T vp0, vp1, vp2;            // velocity parameters
     T t, t_old, t_face;         // time of X, of phi_old, of the faces
     T qscale, qinv;             // deviation storage scale s and 1 / s
+    uint32_t seed;              // step index: the counter of the stochastic rounding
 };
 
 template <typename T>
@@ -288,6 +308,38 @@ __device__ __forceinline__ double block_sum(double v, double *sred) {
     return s;  // valid in thread 0
 }
 
+// 32-bit integer hash (xor-shift / multiply rounds), used as a counter-based
+// source of uniform bits: hash(cell, step) needs no state
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// a + b rounded stochastically to float: the exact sum s + e is found with the
+// error-free two-sum (Knuth), then the neighbour of s on the side of e is taken
+// with probability |e| / |neighbour - s|, so the rounding is unbiased in
+// expectation and small increments are not lost to round-to-nearest
+__device__ __forceinline__ float add_sr(float a, float b, uint32_t bits) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    if (e == 0.0f || s == 0.0f) return s;
+    const int away = (e > 0.0f) == (s > 0.0f) ? 1 : -1;   // step away from or toward zero
+    const float n = __int_as_float(__float_as_int(s) + away);
+    const float u = (float)(bits >> 8) * 0x1p-24f;
+    return u * fabsf(__fsub_rn(n, s)) < fabsf(e) ? n : s;
+}
+
+// the uniform bits of cell (gx, gy) at the step p.seed
+template <typename T>
+__device__ __forceinline__ uint32_t sr_bits(const StepParams<T> &p, int gx, int gy) {
+    return mix32(((uint32_t)gy * (uint32_t)p.nx + (uint32_t)gx) ^ mix32(p.seed));
+}
+
 template <typename ST>
 __device__ __forceinline__ float to_f(ST v);
 template <>
@@ -311,7 +363,8 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
     using TL = Tile<T, ST, ORDER, FLUX, KIND, TX, TY>;
     constexpr int R = TL::R, H = TL::H, WH = TL::WH, WC = TL::WC, WF = TL::WF;
     constexpr int NH = TL::NH, NC = TL::NC, NF = TL::NF;
-    constexpr bool DEV = Store<T, ST>::deviation;
+    constexpr bool DEV = Store<T, ST>::deviation, PHIP = Store<T, ST>::phi_plane;
+    static_assert(KIND == KIND_T2 ? Store<T, ST>::t2 : Store<T, ST>::t3, "scheme not served by this storage");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sX = reinterpret_cast<T *>(smem_raw);  // [9][NH]
@@ -349,7 +402,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
                 sX[k * NH + idx] = v;
                 ph += v;
             }
-            sPhi[idx] = ph;
+            sPhi[idx] = PHIP ? p.phi_cur[g] : ph;
         }
     }
     __syncthreads();
@@ -497,7 +550,11 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             if constexpr (KIND == KIND_T3A) o2[k] = Xk + p.be2 * (gk - Xk) + p.ga2 * L;
             sumL += L;
         }
-        const T phn = (KIND == KIND_T3B ? sumB : ph) + p.ga1 * sumL;
+        T phn;
+        if constexpr (PHIP)   // phi plane: phi + flux sum, rounded without bias
+            phn = add_sr(ph, p.ga1 * sumL, sr_bits(p, gx, gy));
+        else
+            phn = (KIND == KIND_T3B ? sumB : ph) + p.ga1 * sumL;
         {
             T r = T(0);
 #pragma unroll
@@ -518,6 +575,12 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             for (int k = 0; k < 9; k++)
                 put_cell(p, Oq + k * plane, gx, gy,
                          __float2half_rn((o1[k] - wq<T>(k) * phn) * (p.qscale * (T(1) / wq<T>(k)))));
+            put_cell(p, p.phi_out, gx, gy, phn);
+            msum += (double)phn;
+        } else if constexpr (PHIP) {
+            T *O = static_cast<T *>(p.out1);
+#pragma unroll
+            for (int k = 0; k < 9; k++) put_cell(p, O + k * plane, gx, gy, o1[k]);
             put_cell(p, p.phi_out, gx, gy, phn);
             msum += (double)phn;
         } else {
@@ -594,14 +657,15 @@ __global__ void init_kernel(const StepParams<T> p, const T *phi0, T frac_dt) {
         T *O = static_cast<T *>(p.out1);
 #pragma unroll
         for (int k = 0; k < 9; k++) put_cell(p, O + k * plane, gx, gy, fk[k]);
-        put_cell(p, p.phi_out, gx, gy, ph);   // phi of the previous level for d(phi u)/dt
+        // phi plane: phi of X; otherwise phi of the previous level for d(phi u)/dt
+        put_cell(p, p.phi_out, gx, gy, ph);
     }
 }
 
 // sum_k X_k of one cell (the cell's phi), in the storage's arithmetic type
 template <typename T, typename ST>
 __device__ __forceinline__ T cell_phi(const StepParams<T> &p, size_t g) {
-    if constexpr (Store<T, ST>::deviation) {
+    if constexpr (Store<T, ST>::phi_plane) {
         return p.phi_cur[g];
     } else {
         const T *Xf = static_cast<const T *>(p.X);

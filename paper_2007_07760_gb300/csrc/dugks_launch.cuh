@@ -33,19 +33,16 @@ static cudaError_t launch_step_t(const StepParams<T> &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// (each storage compiles only the schemes it serves)
 template <typename T, typename ST, int ORDER, int FLUX>
 static cudaError_t launch_kind(const StepParams<T> &p, int kind, cudaStream_t s) {
-    if constexpr (Store<T, ST>::deviation) {
-        if (kind != KIND_T2) return cudaErrorInvalidValue;
-        return launch_step_t<T, ST, ORDER, FLUX, KIND_T2>(p, s);
-    } else {
-        switch (kind) {
-        case KIND_T2: return launch_step_t<T, ST, ORDER, FLUX, KIND_T2>(p, s);
-        case KIND_T3A: return launch_step_t<T, ST, ORDER, FLUX, KIND_T3A>(p, s);
-        case KIND_T3B: return launch_step_t<T, ST, ORDER, FLUX, KIND_T3B>(p, s);
-        default: return cudaErrorInvalidValue;
-        }
+    if constexpr (Store<T, ST>::t2)
+        if (kind == KIND_T2) return launch_step_t<T, ST, ORDER, FLUX, KIND_T2>(p, s);
+    if constexpr (Store<T, ST>::t3) {
+        if (kind == KIND_T3A) return launch_step_t<T, ST, ORDER, FLUX, KIND_T3A>(p, s);
+        if (kind == KIND_T3B) return launch_step_t<T, ST, ORDER, FLUX, KIND_T3B>(p, s);
     }
+    return cudaErrorInvalidValue;
 }
 
 template <typename T, typename ST, int ORDER>
@@ -223,10 +220,11 @@ template <typename T, typename ST>
 cudaError_t Launch<T, ST>::step_fast4(const StepParams<T> &p, const FaceCoefs<T, 2> &cf, const FastExtra<T> &fe,
                                       const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc,
                                       int flux, int kind, cudaStream_t s) {
-    if (kind == KIND_T2)
-        return flux == 0 ? launch_fast4_t<T, ST, 0, KIND_T2>(p, cf, fe, tmX, tmPo, tmPc, s)
-                         : launch_fast4_t<T, ST, 1, KIND_T2>(p, cf, fe, tmX, tmPo, tmPc, s);
-    if constexpr (!Store<T, ST>::deviation) {
+    if constexpr (Store<T, ST>::t2)
+        if (kind == KIND_T2)
+            return flux == 0 ? launch_fast4_t<T, ST, 0, KIND_T2>(p, cf, fe, tmX, tmPo, tmPc, s)
+                             : launch_fast4_t<T, ST, 1, KIND_T2>(p, cf, fe, tmX, tmPo, tmPc, s);
+    if constexpr (Store<T, ST>::t3) {
         if (kind == KIND_T3A)
             return flux == 0 ? launch_fast4_t<T, ST, 0, KIND_T3A>(p, cf, fe, tmX, tmPo, tmPc, s)
                              : launch_fast4_t<T, ST, 1, KIND_T3A>(p, cf, fe, tmX, tmPo, tmPc, s);

@@ -1,9 +1,24 @@
 """Accuracy of every precision against the FP64 oracle on the slotted-disk
-rotation (256 x 256, order-3 upwind, two-stage, M = 0.002, cfl = 0.8), 2000
-steps: max |dphi|, relative L2 difference and mass drift, each printed (run
-pytest with -s to see the line) and bounded: FP64 1e-12 relative, FP32 5e-5
-max |dphi| (the FP32 acceptance bound), FP16 storage 2e-3.
+rotation (256 x 256, order-3 upwind, two-stage, M = 0.002, cfl = 0.8) after
+2000 steps and after the full revolution (16384 steps): max |dphi|, relative L2
+difference and mass drift, each printed (run pytest with -s to see the line)
+and bounded: FP64 1e-12 relative (5e-6 after the revolution, see below), FP32
+and FP16 storage 5e-5 max |dphi| (the FP32 acceptance bound) at both lengths.
+
+Over the second half of the revolution the discrete problem itself amplifies
+perturbations: the over- and undershoots the sharp slot corners leave (phi a
+little above 1 or below 0) are where theta = -(phi - 1) phi changes sign and the
+interface term stops sharpening. A perturbation of 1e-15 in phi0 grows to about
+1e-13 by step 4000 and to about 6e-7 by step 16384 (the conditioning test below
+measures it on the GPU; the oracle shows the same growth), so two FP64
+implementations that differ only in rounding order agree to that level there.
+
+The two-stage FP32 and FP16 storage paths keep phi as a plane of its own and
+add each step's flux sum with unbiased stochastic rounding; rounding to nearest
+there loses increments below half an ulp of phi in the same direction step after
+step, and over the revolution that alone exceeded the bound.
 """
+import dataclasses
 import json
 
 import numpy as np
@@ -14,7 +29,7 @@ from paper_2007_07760_gb300 import workloads as WL
 
 pytestmark = pytest.mark.gpu
 
-STEPS = 2000
+LENGTHS = (2000, 16384)
 
 
 @pytest.fixture(scope="module")
@@ -24,26 +39,62 @@ def reference(oracle):
                       stages=prob.stages, dtphiu=prob.dtphiu, vel_kind=prob.vel_kind, vel=prob.vel)
     st = oracle.State(p, prob.phi0)
     m0 = st.mass()
-    st.run(STEPS)
-    return prob, st.phi(), m0, st.mass()
+    snaps = {}
+    for n in LENGTHS:
+        st.run(n - st.step_index)
+        snaps[n] = (st.phi(), st.mass())
+    return prob, m0, snaps
 
 
-@pytest.mark.parametrize("precision,bound", [("fp64", 1e-12), ("fp32", 5e-5), ("fp16f", 2e-3)])
-def test_precision_against_oracle(reference, precision, bound):
-    prob, ref, m0_ref, m_ref = reference
-    with N.Solver.from_problem(prob, precision=precision) as s:
-        m0 = s.mass()
-        s.step(STEPS)
-        phi = s.phi()
-        m = s.mass()
-        assert s.status() == 0
+@pytest.fixture(scope="module")
+def runs(reference):
+    prob = reference[0]
+    out = {}
+    for precision in ("fp64", "fp32", "fp16f"):
+        with N.Solver.from_problem(prob, precision=precision) as s:
+            m0 = s.mass()
+            for n in LENGTHS:
+                s.step(n - s.step_index)
+                out[precision, n] = (s.phi(), s.mass(), m0)
+            assert s.status() == 0
+    return out
+
+
+@pytest.mark.parametrize("steps", LENGTHS)
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16f"])
+def test_precision_against_oracle(reference, runs, precision, steps):
+    _, m0_ref, snaps = reference
+    ref, m_ref = snaps[steps]
+    phi, m, m0 = runs[precision, steps]
     d = phi - ref
-    rep = {"precision": precision, "steps": STEPS, "max_abs_dphi": float(np.abs(d).max()),
+    rep = {"precision": precision, "steps": steps, "max_abs_dphi": float(np.abs(d).max()),
            "rel_l2_dphi": float(np.sqrt((d ** 2).sum() / (ref ** 2).sum())),
            "mass_drift": float(abs(m - m0) / m0), "oracle_mass_drift": float(abs(m_ref - m0_ref) / m0_ref)}
     print("ACCURACY", json.dumps(rep))
     if precision == "fp64":
-        assert rep["max_abs_dphi"] / np.abs(ref).max() < bound
+        assert rep["max_abs_dphi"] / np.abs(ref).max() < (1e-12 if steps <= 2000 else 5e-6)
+        assert rep["mass_drift"] < 1e-12
     else:
-        assert rep["max_abs_dphi"] < bound
-    assert rep["mass_drift"] < (1e-12 if precision == "fp64" else 1e-5)
+        assert rep["max_abs_dphi"] < 5e-5
+        assert rep["mass_drift"] < 1e-6
+
+
+def test_conditioning_of_the_revolution(reference):
+    """Perturbing phi0 by 1e-15 (seeded normal) changes the FP64 result by
+    little at 2000 steps and by orders of magnitude more after the revolution:
+    the FP64 tolerance after 16384 steps is set by this growth, not by the
+    implementation."""
+    prob = reference[0]
+    rng = np.random.default_rng(WL.SEED_BASE + 15)
+    pert = dataclasses.replace(prob, phi0=prob.phi0 + 1e-15 * rng.standard_normal(prob.phi0.shape))
+    out = {}
+    for name, pr in (("base", prob), ("perturbed", pert)):
+        with N.Solver.from_problem(pr, precision="fp64") as s:
+            for n in LENGTHS:
+                s.step(n - s.step_index)
+                out[name, n] = s.phi()
+            assert s.status() == 0
+    g = {n: float(np.abs(out["base", n] - out["perturbed", n]).max()) for n in LENGTHS}
+    print("CONDITIONING", json.dumps(g))
+    assert g[2000] < 1e-11
+    assert 1e-9 < g[16384] < 5e-6
