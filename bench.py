@@ -6,7 +6,7 @@ W = 4, cfl = 0.8, amplitude 0.05, reversal period 8192 steps). One benchmark
 step = one pass of the whole hot path: the fused DUGKS step kernel (cell
 quantities, gradients, face reconstruction, face distribution, meso-flux
 update, per-tile FP64 mass partials) plus the global FP64 mass reduction. The
-state (84 MB) fits in L2, so L2 is flushed (512 MiB write) before every timed
+state (92 MB) fits in L2, so L2 is flushed (512 MiB write) before every timed
 step and only the step itself is timed, with CUDA events on the solver's stream.
 
 Beside the main line (N = 1 only) the same JSON line carries, under "also", the
@@ -49,7 +49,7 @@ L2_FLUSH_BYTES = 512 << 20
 # writes of a 1024^2 step stay in L2 (129 MB) during the launch and reach DRAM
 # later, so the figure is the read traffic plus the evictions.
 NCU_TRAFFIC = {
-    ("9508ee7cfda1ab6d", "vortex1024_fp32_p3_upwind_2stage"): 46400512,
+    ("036aa89b17aa8597", "vortex1024_fp32_p3_upwind_2stage"): 51917312,
 }
 
 
