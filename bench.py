@@ -282,7 +282,7 @@ def also_single(name: str, precision: str, K: int, generic: bool = False):
         r = time_single(solver, stream, 10, K)
     peak, _ = measured_peak_hbm()
     # the three-stage scheme runs two kernels per step, which move 56 values per cell between them
-    bpc = BYTES_PER_CELL[precision] if prob.stages == 2 else {"fp64": 448, "fp32": 224}[precision]
+    bpc = BYTES_PER_CELL[precision] if prob.stages == 2 else {"fp64": 456, "fp32": 248}[precision]
     achieved = bpc * prob.cells / (r["avg_step_ms"] * 1e-3) / 1e9
     return {"workload": desc["workload"] + ("_generic_kernel" if generic else ""), "bytes_per_cell": bpc,
             "value": prob.cells * K / (r["total_ms"] * 1e-3), "unit": UNIT, "steps": K,

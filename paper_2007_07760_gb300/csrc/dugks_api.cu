@@ -32,7 +32,7 @@ struct dugks_ctx {
     size_t tsize = 8, ssize = 8;
     int nsets = 2, nphi = 2;
     void *X[3] = {nullptr, nullptr, nullptr};
-    void *phi[3] = {nullptr, nullptr, nullptr};
+    void *phi[4] = {nullptr, nullptr, nullptr, nullptr};
     int cur = 0;                // current state set (two-stage)
     int pr[3] = {0, 1, 2};      // phi plane roles (see step_t2 / step_t3)
     void *phi0 = nullptr;       // initial phi (T, plane layout)
@@ -45,7 +45,7 @@ struct dugks_ctx {
     // TMA-staged two-stage path (orders 2, 3)
     bool fast = false;
     int variant = 0;
-    CUtensorMap tmX[2], tmPhi[3];
+    CUtensorMap tmX[2], tmPhi[4];
     double coef_h = -1.0;
     std::vector<unsigned char> coefs;   // FaceCoefs<T> of the current h
     double coef3_dt = -1.0;             // three-stage: FaceCoefs<T> at dt / 6 and 5 dt / 12
@@ -170,7 +170,7 @@ int ensure_init(dugks_ctx *c) {
     if (c->initialized) return DUGKS_OK;
     switch (c->p.precision) {
     case DUGKS_FP64: return run_init<double, double>(c);
-    case DUGKS_FP32: return c->p.stages == 3 ? run_init<float, float>(c) : run_init<float, PhiF32>(c);
+    case DUGKS_FP32: return run_init<float, float>(c);
     default: return run_init<float, __half>(c);
     }
 }
@@ -268,6 +268,7 @@ int step_t2(dugks_ctx *c) {
 // X[2] = accumulator f^n + (3 dt / 7) L*.
 template <typename T>
 int step_t3(dugks_ctx *c) {
+    constexpr bool PHIP = Store<T, T>::phi_plane;
     const double dt = c->p.cfl, tau = 3.0 * c->p.M;
     const double t = (double)c->step * dt;
     // (i)-(ii): bar f^{+, dt/6} (Eq. (31)), flux at t_n + dt/6, tilde f(t') and accumulator
@@ -290,8 +291,23 @@ int step_t3(dugks_ctx *c) {
     A.X = c->X[0];
     A.out1 = c->X[1];
     A.out2 = static_cast<T *>(c->X[2]);
-    A.phi_old = static_cast<const T *>(c->phi[c->pr[0]]);
-    A.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
+    A.seed = (uint32_t)(2 * c->step);
+    // phi planes (FP32): pr0 = phi^n (of X), pr1 = phi^{n-1}; plane 2 receives phi of
+    // tilde f', plane 3 phi of the accumulator, and kernel B writes phi^{n+1} over
+    // pr1. Otherwise (FP64): pr0 = phi^{n-1}; kernel A writes phi^n to pr1.
+    int aPo = c->pr[0], aPc = c->pr[0], bPo = c->pr[1], bPc = c->pr[1];
+    if (PHIP) {
+        aPc = c->pr[0];
+        aPo = c->pr[1];
+        bPc = 2;
+        bPo = c->pr[0];
+        A.phi_cur = static_cast<const T *>(c->phi[aPc]);
+        A.phi_out = static_cast<T *>(c->phi[2]);
+        A.phi_out2 = static_cast<T *>(c->phi[3]);
+    } else {
+        A.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
+    }
+    A.phi_old = static_cast<const T *>(c->phi[aPo]);
     cudaError_t e;
     if (c->fast && c->coef3_dt != dt) {
         auto keep = [](std::vector<unsigned char> &v, const auto &cf) {
@@ -308,12 +324,12 @@ int step_t3(dugks_ctx *c) {
     }
     if (c->fast && c->p.order == 4) {
         e = Launch<T, T>::step_fast4(A, *reinterpret_cast<const FaceCoefs<T, 2> *>(c->coefs3[0].data()),
-                                     vortex_factors<T>(c, t, t - dt, t + dt / 6.0), c->tmX[0], c->tmPhi[c->pr[0]],
-                                     c->tmPhi[c->pr[0]], c->p.flux, KIND_T3A, c->stream);
+                                     vortex_factors<T>(c, t, t - dt, t + dt / 6.0), c->tmX[0], c->tmPhi[aPo],
+                                     c->tmPhi[aPc], c->p.flux, KIND_T3A, c->stream);
     } else if (c->fast) {
         const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs3[0].data());
         e = Launch<T, T>::step_fast3(A, cf, vortex_factors<T>(c, t, t - dt, t + dt / 6.0), c->tmX[0],
-                                     c->tmPhi[c->pr[0]], c->p.order, c->p.flux, KIND_T3A, c->stream);
+                                     c->tmPhi[aPo], c->tmPhi[aPc], c->p.order, c->p.flux, KIND_T3A, c->stream);
     } else {
         e = Launch<T, T>::step(A, c->p.order, c->p.flux, KIND_T3A, c->stream);
     }
@@ -336,16 +352,22 @@ int step_t3(dugks_ctx *c) {
     B.X = c->X[1];
     B.acc = c->X[2];
     B.out1 = c->X[0];
-    B.phi_old = static_cast<const T *>(c->phi[c->pr[1]]);
+    B.seed = (uint32_t)(2 * c->step + 1);
+    B.phi_old = static_cast<const T *>(c->phi[bPo]);
+    if (PHIP) {
+        B.phi_cur = static_cast<const T *>(c->phi[bPc]);
+        B.phi_acc = static_cast<const T *>(c->phi[3]);
+        B.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
+    }
     B.mass_partial = c->partial;
     if (c->fast && c->p.order == 4) {
         e = Launch<T, T>::step_fast4(B, *reinterpret_cast<const FaceCoefs<T, 2> *>(c->coefs3[1].data()),
                                      vortex_factors<T>(c, t + dt / 3.0, t, t + 0.75 * dt), c->tmX[1],
-                                     c->tmPhi[c->pr[1]], c->tmPhi[c->pr[1]], c->p.flux, KIND_T3B, c->stream);
+                                     c->tmPhi[bPo], c->tmPhi[bPc], c->p.flux, KIND_T3B, c->stream);
     } else if (c->fast) {
         const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs3[1].data());
         e = Launch<T, T>::step_fast3(B, cf, vortex_factors<T>(c, t + dt / 3.0, t, t + 0.75 * dt), c->tmX[1],
-                                     c->tmPhi[c->pr[1]], c->p.order, c->p.flux, KIND_T3B, c->stream);
+                                     c->tmPhi[bPo], c->tmPhi[bPc], c->p.order, c->p.flux, KIND_T3B, c->stream);
     } else {
         e = Launch<T, T>::step(B, c->p.order, c->p.flux, KIND_T3B, c->stream);
     }
@@ -361,7 +383,7 @@ int step_once(dugks_ctx *c) {
     } else {
         switch (c->p.precision) {
         case DUGKS_FP64: r = step_t2<double, double>(c); break;
-        case DUGKS_FP32: r = step_t2<float, PhiF32>(c); break;
+        case DUGKS_FP32: r = step_t2<float, float>(c); break;
         default: r = step_t2<float, __half>(c); break;
         }
     }
@@ -386,10 +408,7 @@ int enqueue_mass(dugks_ctx *c, double *dev_out) {
     if (!c->mass_valid) {
         switch (c->p.precision) {
         case DUGKS_FP64: e = Launch<double, double>::mass_partial(state_view<double, double>(c), c->stream); break;
-        case DUGKS_FP32:
-            e = c->p.stages == 3 ? Launch<float, float>::mass_partial(state_view<float, float>(c), c->stream)
-                                 : Launch<float, PhiF32>::mass_partial(state_view<float, PhiF32>(c), c->stream);
-            break;
+        case DUGKS_FP32: e = Launch<float, float>::mass_partial(state_view<float, float>(c), c->stream); break;
         default: e = Launch<float, __half>::mass_partial(state_view<float, __half>(c), c->stream); break;
         }
         if (e != cudaSuccess) return cuda_fail(c, e, "mass partial kernel");
@@ -404,11 +423,7 @@ int enqueue_phi(dugks_ctx *c, void *dev_out) {
     cudaError_t e;
     switch (c->p.precision) {
     case DUGKS_FP64: e = Launch<double, double>::phi(state_view<double, double>(c), static_cast<double *>(dev_out), c->stream); break;
-    case DUGKS_FP32:
-        e = c->p.stages == 3
-                ? Launch<float, float>::phi(state_view<float, float>(c), static_cast<float *>(dev_out), c->stream)
-                : Launch<float, PhiF32>::phi(state_view<float, PhiF32>(c), static_cast<float *>(dev_out), c->stream);
-        break;
+    case DUGKS_FP32: e = Launch<float, float>::phi(state_view<float, float>(c), static_cast<float *>(dev_out), c->stream); break;
     default: e = Launch<float, __half>::phi(state_view<float, __half>(c), static_cast<float *>(dev_out), c->stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "phi kernel");
@@ -422,7 +437,7 @@ int sync_ctx(dugks_ctx *c) {
 }
 
 void free_ctx(dugks_ctx *c) {
-    for (void *q : {c->X[0], c->X[1], c->X[2], c->phi[0], c->phi[1], c->phi[2], c->phi0, c->ufield,
+    for (void *q : {c->X[0], c->X[1], c->X[2], c->phi[0], c->phi[1], c->phi[2], c->phi[3], c->phi0, c->ufield,
                     c->vfield, c->tmp, (void *)c->partial, (void *)c->dmass, (void *)c->dstatus})
         if (q) cudaFree(q);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -514,8 +529,10 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     c->pitch = (p->nx + 2 * GHOST + 31) / 32 * 32;
     c->plane = (size_t)(p->ny + 2 * GHOST) * c->pitch;
     c->nsets = p->stages == 3 ? 3 : 2;
-    // two-stage FP32 and FP16F keep phi as a plane of its own: three rotating roles
-    c->nphi = (p->precision == DUGKS_FP16F || (p->precision == DUGKS_FP32 && p->stages == 2)) ? 3 : 2;
+    // FP32 and FP16F keep phi as a plane of its own: three rotating roles (two-stage), or
+    // the state's and the previous level's plus phi of tilde f' and of the accumulator
+    // (three-stage); FP64: the previous level for d(phi u)/dt (and phi^n, three-stage)
+    c->nphi = p->precision == DUGKS_FP64 ? 2 : p->stages == 3 ? 4 : 3;
     // the TMA-staged kernels serve every order and both schemes (three-stage: full
     // storage; order 4 and the three-stage scheme: one tile shape, 8 x 2)
     c->fast = (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
@@ -544,7 +561,7 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     if (ok) ok = cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
     if (ok && c->fast) {
         bool enc = p->precision == DUGKS_FP64 ? setup_fast<double, double>(c)
-                   : p->precision == DUGKS_FP32 ? (p->stages == 3 ? setup_fast<float, float>(c) : setup_fast<float, PhiF32>(c))
+                   : p->precision == DUGKS_FP32 ? setup_fast<float, float>(c)
                                                 : setup_fast<float, __half>(c);
         if (!enc) {   // use the generic CUDA kernel instead
             c->fast = false;
@@ -655,11 +672,7 @@ int dugks_read_phi(dugks_ctx *c, double *out_host) {
     cudaError_t e;
     switch (c->p.precision) {
     case DUGKS_FP64: e = Launch<double, double>::phi64(state_view<double, double>(c), static_cast<double *>(c->tmp), c->stream); break;
-    case DUGKS_FP32:
-        e = c->p.stages == 3
-                ? Launch<float, float>::phi64(state_view<float, float>(c), static_cast<double *>(c->tmp), c->stream)
-                : Launch<float, PhiF32>::phi64(state_view<float, PhiF32>(c), static_cast<double *>(c->tmp), c->stream);
-        break;
+    case DUGKS_FP32: e = Launch<float, float>::phi64(state_view<float, float>(c), static_cast<double *>(c->tmp), c->stream); break;
     default: e = Launch<float, __half>::phi64(state_view<float, __half>(c), static_cast<double *>(c->tmp), c->stream); break;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "phi kernel");
@@ -742,7 +755,7 @@ int dugks_set_variant(dugks_ctx *c, int variant) {
         c->fast = true;
         c->variant = variant;
         const bool ok = c->p.precision == DUGKS_FP64 ? setup_fast<double, double>(c)
-                        : c->p.precision == DUGKS_FP32 ? (c->p.stages == 3 ? setup_fast<float, float>(c) : setup_fast<float, PhiF32>(c))
+                        : c->p.precision == DUGKS_FP32 ? setup_fast<float, float>(c)
                                                        : setup_fast<float, __half>(c);
         if (!ok) return fail(c, DUGKS_ECUDA, "tensor map encoding failed");
     }
@@ -768,7 +781,7 @@ const char *dugks_last_error(const dugks_ctx *c) { return c ? c->err.c_str() : "
 int64_t dugks_step_index(const dugks_ctx *c) { return c ? c->step : -1; }
 
 // phi of the state and of the previous level where phi is a plane of its own
-static int saved_phi_planes(const dugks_ctx *c) { return c->nphi == 3 ? 2 : 1; }
+static int saved_phi_planes(const dugks_ctx *c) { return c->p.precision == DUGKS_FP64 ? 1 : 2; }
 
 size_t dugks_state_bytes(const dugks_ctx *c) {
     if (!c) return 0;

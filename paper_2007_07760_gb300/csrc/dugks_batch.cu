@@ -92,7 +92,7 @@ FastGeom geom(const dugks_batch *b) { return Launch<T, ST>::fast_geom(b->variant
 FastGeom batch_geom(const dugks_batch *b) {
     switch (b->p.precision) {
     case DUGKS_FP64: return geom<double, double>(b);
-    case DUGKS_FP32: return geom<float, PhiF32>(b);
+    case DUGKS_FP32: return geom<float, float>(b);
     default: return geom<float, __half>(b);
     }
 }
@@ -103,7 +103,7 @@ int resident_ctas(dugks_batch *b) {
     int per = 1;
     switch (b->p.precision) {
     case DUGKS_FP64: per = Launch<double, double>::batch_ctas_per_sm(b->p.order, b->p.flux, b->variant); break;
-    case DUGKS_FP32: per = Launch<float, PhiF32>::batch_ctas_per_sm(b->p.order, b->p.flux, b->variant); break;
+    case DUGKS_FP32: per = Launch<float, float>::batch_ctas_per_sm(b->p.order, b->p.flux, b->variant); break;
     default: per = Launch<float, __half>::batch_ctas_per_sm(b->p.order, b->p.flux, b->variant); break;
     }
     return std::max(1, sms) * std::max(1, per);
@@ -235,7 +235,7 @@ int rebuild_t(dugks_batch *b) {
 int rebuild(dugks_batch *b) {
     switch (b->p.precision) {
     case DUGKS_FP64: return rebuild_t<double, double>(b);
-    case DUGKS_FP32: return rebuild_t<float, PhiF32>(b);
+    case DUGKS_FP32: return rebuild_t<float, float>(b);
     default: return rebuild_t<float, __half>(b);
     }
 }
@@ -254,7 +254,7 @@ cudaError_t launch_one_step(dugks_batch *b) {
 cudaError_t one_step(dugks_batch *b) {
     switch (b->p.precision) {
     case DUGKS_FP64: return launch_one_step<double, double>(b);
-    case DUGKS_FP32: return launch_one_step<float, PhiF32>(b);
+    case DUGKS_FP32: return launch_one_step<float, float>(b);
     default: return launch_one_step<float, __half>(b);
     }
 }
@@ -418,7 +418,7 @@ int dugks_batch_add(dugks_batch *b, int32_t nx, int32_t ny, const double *phi0_h
     int r;
     switch (b->p.precision) {
     case DUGKS_FP64: r = init_slot<double, double>(b, s, phi0_host); break;
-    case DUGKS_FP32: r = init_slot<float, PhiF32>(b, s, phi0_host); break;
+    case DUGKS_FP32: r = init_slot<float, float>(b, s, phi0_host); break;
     default: r = init_slot<float, __half>(b, s, phi0_host); break;
     }
     if (r != DUGKS_OK) {
@@ -526,7 +526,7 @@ int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host) {
     double *d = static_cast<double *>(b->d_tmp);
     switch (b->p.precision) {
     case DUGKS_FP64: e = Launch<double, double>::phi64(slot_view<double, double>(b, s), d, b->stream); break;
-    case DUGKS_FP32: e = Launch<float, PhiF32>::phi64(slot_view<float, PhiF32>(b, s), d, b->stream); break;
+    case DUGKS_FP32: e = Launch<float, float>::phi64(slot_view<float, float>(b, s), d, b->stream); break;
     default: e = Launch<float, __half>::phi64(slot_view<float, __half>(b, s), d, b->stream); break;
     }
     if (e != cudaSuccess) return bcuda(b, e, "phi kernel");
@@ -561,7 +561,7 @@ int dugks_batch_mass(dugks_batch *b, int32_t grid_id, double *out) {
         double *part = static_cast<double *>(b->d_tmp), *res = part + tiles;
         switch (b->p.precision) {
         case DUGKS_FP64: { auto q = slot_view<double, double>(b, s); q.mass_partial = part; e = Launch<double, double>::mass_partial(q, b->stream); break; }
-        case DUGKS_FP32: { auto q = slot_view<float, PhiF32>(b, s); q.mass_partial = part; e = Launch<float, PhiF32>::mass_partial(q, b->stream); break; }
+        case DUGKS_FP32: { auto q = slot_view<float, float>(b, s); q.mass_partial = part; e = Launch<float, float>::mass_partial(q, b->stream); break; }
         default: { auto q = slot_view<float, __half>(b, s); q.mass_partial = part; e = Launch<float, __half>::mass_partial(q, b->stream); break; }
         }
         if (e == cudaSuccess) e = launch_mass_final(part, tiles, res, b->d_status, b->stream);

@@ -246,8 +246,10 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
     // KIND_T2: the two-stage step. KIND_T3A / KIND_T3B: the two kernels of the
     // three-stage step (Sec. II.B.2), full storage only:
     //   T3A  out1 = X + be1 (g - X) + ga1 L (tilde f at t'), out2 = X + be2 (g - X) + ga2 L
-    //        (the accumulator, in T), phi_out = phi of X;
-    //   T3B  out1 = acc + be1 (g - X) + ga1 L (hat f at t_n + dt; al1 = -be1), mass partial.
+    //        (the accumulator, in T); phi_out = phi of X, or with phi planes phi of out1
+    //        (phi_out) and of out2 (phi_out2);
+    //   T3B  out1 = acc + be1 (g - X) + ga1 L (hat f at t_n + dt; al1 = -be1), mass partial;
+    //        with phi planes phi of acc from phi_acc and phi of out1 to phi_out.
     static_assert(KIND == KIND_T2 ? Store<T, ST>::t2 : Store<T, ST>::t3, "scheme not served by this storage");
     constexpr bool T3A = KIND == KIND_T3A, T3B = KIND == KIND_T3B;
 
@@ -594,14 +596,18 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
         const T dVNx = T(0.5) * (sV[cj + CW] - sV[cj - CW]), dVNy = T(0.5) * (sV[NC + cj + CW] - sV[NC + cj - CW]);
         if constexpr (KIND != KIND_T2) {
             // out = part_k - w_k (xi_x A1 + xi_y A2 + xi_x^2 B1 + xi_x xi_y B2 + xi_y^2 B3), all scaled
-            // by the output's gamma; its rest component from phi_base + gamma sum_k L_k
-            auto combine = [&](T gam, T gmcX, T phib, auto part, T (&o)[9]) -> T {
+            // by the output's gamma; its rest component from phi_base + gamma sum_k L_k (a phi
+            // plane: that sum added with stochastic rounding, uniform bits `bits`)
+            auto combine = [&](T gam, T gmcX, T phib, auto part, T (&o)[9], uint32_t bits) -> T {
                 const T g2 = gam * p.c2, g3 = gam * p.c3;
                 const T A1 = g2 * dE[0], A2 = g2 * dN[0];
                 const T B1 = T(3) * g2 * dE[1] + g3 * dVEx;
                 const T B2 = T(3) * g2 * (dE[2] + dN[1]) + g3 * (dVEy + dVNx);
                 const T B3 = T(3) * g2 * dN[2] + g3 * dVNy;
-                const T ph = phib - gmcX * sumD[r] - (B1 + B3) * T(1.0 / 3.0);
+                const T dph = -gmcX * sumD[r] - (B1 + B3) * T(1.0 / 3.0);
+                T ph;
+                if constexpr (PHIP) ph = add_sr(phib, dph, bits);
+                else ph = phib + dph;
                 const T S13 = B1 + B3;
                 o[1] = part(1) - wq<T>(1) * (A1 + B1);
                 o[5] = part(5) - wq<T>(5) * (B1 - A1);
@@ -621,27 +627,34 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             const size_t g = gidx(p, gx, gy);
             T *O = static_cast<T *>(p.out1);
             T o[9];
+            const uint32_t bits = PHIP ? sr_bits(p, gx, gy) : 0u;
             if constexpr (T3A) {
-                combine(p.ga1, gmc, cg[r], [&](int k) { return part_ref(k, r); }, o);
+                // phi plane: phi of tilde f' (with ghosts: kernel B stages it) and of the
+                // accumulator; otherwise phi of X (the older level of kernel B's d(phi u)/dt)
+                const T ph1 = combine(p.ga1, gmc, cg[r], [&](int k) { return part_ref(k, r); }, o, bits);
+                const T pho = PHIP ? ph1 : cg[r];
 #pragma unroll
                 for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
-                p.phi_out[g] = cg[r];
-                if (edge) put_ghosts9(p, O, gx, gy, cg[r], o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
+                p.phi_out[g] = pho;
+                if (edge) put_ghosts9(p, O, gx, gy, pho, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
                 T o2[9];
-                combine(p.ga2, gmc2, cg[r], [&](int k) { return part2_ref(k, r); }, o2);
+                const T ph2 = combine(p.ga2, gmc2, cg[r], [&](int k) { return part2_ref(k, r); }, o2, mix32(bits));
 #pragma unroll
                 for (int k = 0; k < 9; k++) p.out2[k * plane + g] = o2[k];   // read per cell only: no ghosts
+                if constexpr (PHIP) p.phi_out2[g] = ph2;
             } else {
                 const T *Acc = static_cast<const T *>(p.acc);
                 T a[9], pha = T(0);
 #pragma unroll
                 for (int k = 0; k < 9; k++) {
                     a[k] = Acc[k * plane + g];
-                    pha += a[k];
+                    if constexpr (!PHIP) pha += a[k];
                 }
-                const T phn = combine(p.ga1, gmc, pha, [&](int k) { return a[k] + part_ref(k, r); }, o);
+                if constexpr (PHIP) pha = p.phi_acc[g];
+                const T phn = combine(p.ga1, gmc, pha, [&](int k) { return a[k] + part_ref(k, r); }, o, bits);
 #pragma unroll
                 for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
+                if constexpr (PHIP) p.phi_out[g] = phn;   // phi^{n+1} (else phi_out is null)
                 if (edge) put_ghosts9(p, O, gx, gy, phn, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
                 msum += (double)phn;
             }

@@ -1,9 +1,9 @@
-// many-grid step and advance kernels; state and arithmetic in float, phi a plane of its own.
+// many-grid step and advance kernels; state and arithmetic in float.
 // (One translation unit per precision and kernel family, so they compile in parallel.)
 #include "dugks_launch.cuh"
 
 namespace dugks {
-template cudaError_t Launch<float,PhiF32>::batch_step(const BatchUniform<float> &, const FaceCoefs<float> &, const BatchGrid<float> *, const int4 *, int, double *, int, int, int, int, cudaStream_t);
-template int Launch<float,PhiF32>::batch_ctas_per_sm(int, int, int);
+template cudaError_t Launch<float,float>::batch_step(const BatchUniform<float> &, const FaceCoefs<float> &, const BatchGrid<float> *, const int4 *, int, double *, int, int, int, int, cudaStream_t);
+template int Launch<float,float>::batch_ctas_per_sm(int, int, int);
 template cudaError_t launch_batch_advance<float>(BatchGrid<float> *, int, const double *, double *, int *, cudaStream_t);
 }  // namespace dugks

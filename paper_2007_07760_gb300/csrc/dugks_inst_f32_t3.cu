@@ -3,5 +3,5 @@
 #include "dugks_launch.cuh"
 
 namespace dugks {
-template cudaError_t Launch<float,float>::step_fast3(const StepParams<float> &, const FaceCoefs<float> &, const FastExtra<float> &, const CUtensorMap &, const CUtensorMap &, int, int, int, cudaStream_t);
+template cudaError_t Launch<float,float>::step_fast3(const StepParams<float> &, const FaceCoefs<float> &, const FastExtra<float> &, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, int, int, int, cudaStream_t);
 }  // namespace dugks

@@ -3,5 +3,5 @@
 #include "dugks_launch.cuh"
 
 namespace dugks {
-template cudaError_t Launch<double,double>::step_fast3(const StepParams<double> &, const FaceCoefs<double> &, const FastExtra<double> &, const CUtensorMap &, const CUtensorMap &, int, int, int, cudaStream_t);
+template cudaError_t Launch<double,double>::step_fast3(const StepParams<double> &, const FaceCoefs<double> &, const FastExtra<double> &, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, int, int, int, cudaStream_t);
 }  // namespace dugks

@@ -50,10 +50,11 @@ struct Launch {
                                   const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc, int flux,
                                   int kind, cudaStream_t s);
     // one kernel of the three-stage step (kind KIND_T3A or KIND_T3B) on the TMA-staged
-    // path, tile 8 warps x 2 rows (full storage only: ST == T)
+    // path, tile 8 warps x 2 rows (full storage only: ST == T); tmPc maps the plane of
+    // phi of X where phi is a plane of its own (FP32)
     static cudaError_t step_fast3(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,
-                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, int order, int flux, int kind,
-                                  cudaStream_t s);
+                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc, int order,
+                                  int flux, int kind, cudaStream_t s);
 };
 
 template <typename T>

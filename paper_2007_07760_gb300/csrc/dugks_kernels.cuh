@@ -43,32 +43,24 @@ __host__ __device__ __forceinline__ constexpr T wq(int k) {
 enum Kind { KIND_T2 = 0, KIND_T3A = 1, KIND_T3B = 2 };
 enum Vel { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_FIELD = 3 };
 
-// FP32 full values of the two-stage scheme whose phi is its own plane (the
-// storage tag of that layout; converts to float on reads)
-struct PhiF32 {
-    float v;
-    __host__ __device__ operator float() const { return v; }
-};
-
 // Storage of the distribution and of phi:
-//  * Store<T, T>: full values of type T; phi of a state is sum_k X_k
-//    (FP64, both schemes; FP32 three-stage)
-//  * Store<float, PhiF32>: full FP32 values plus phi as an FP32 plane of its own,
-//    updated by phi + sum of the face fluxes with unbiased stochastic rounding
-//    (FP32 two-stage); sum_k X_k equals that phi up to rounding
+//  * Store<double, double>: full FP64 values; phi of a state is sum_k X_k
+//  * Store<float, float>: full FP32 values plus phi as an FP32 plane of its own,
+//    updated by phi + sum of the face fluxes with unbiased stochastic rounding;
+//    sum_k X_k equals that phi up to rounding
 //  * Store<float, __half>: half-precision scaled deviations
-//    q_k = (f_k - w_k phi) * s / w_k, phi likewise its own plane (FP16F, two-stage)
-// phi_plane: phi is read from and written to its plane (roles rotate over three
-// planes) rather than summed; t2 / t3: the schemes that storage serves.
+//    q_k = (f_k - w_k phi) * s / w_k, phi likewise its own plane (two-stage only)
+// phi_plane: phi is read from and written to its planes rather than summed;
+// t2 / t3: the schemes that storage serves.
 template <typename T, typename ST>
 struct Store;
-template <typename T>
-struct Store<T, T> {
-    static constexpr bool deviation = false, phi_plane = false, t2 = sizeof(T) == 8, t3 = true;
+template <>
+struct Store<double, double> {
+    static constexpr bool deviation = false, phi_plane = false, t2 = true, t3 = true;
 };
 template <>
-struct Store<float, PhiF32> {
-    static constexpr bool deviation = false, phi_plane = true, t2 = true, t3 = false;
+struct Store<float, float> {
+    static constexpr bool deviation = false, phi_plane = true, t2 = true, t3 = true;
 };
 template <>
 struct Store<float, __half> {
@@ -92,7 +84,9 @@ struct StepParams {
     const void *acc;            // KIND_T3B: accumulator planes (type T)
     const T *phi_cur;           // deviation storage: phi of X (authoritative)
     const T *phi_old;           // phi at the older time level of d(phi u)/dt
-    T *phi_out;                 // T2/T3A: phi of X; deviation storage: phi of out1
+    T *phi_out;                 // phi plane: phi of out1; otherwise (T2/T3A) phi of X
+    T *phi_out2;                // phi plane, T3A: phi of out2 (the accumulator)
+    const T *phi_acc;           // phi plane, T3B: phi of the accumulator
     void *out1;                 // 9 planes (storage type for T2/T3B, T for T3A)
     T *out2;                    // KIND_T3A: accumulator planes
     double *mass_partial;       // per-CTA sum of phi of out1 (T2, T3B), may be null
@@ -550,9 +544,12 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             if constexpr (KIND == KIND_T3A) o2[k] = Xk + p.be2 * (gk - Xk) + p.ga2 * L;
             sumL += L;
         }
+        // phi planes: the base phi (T3B: the accumulator's, from its plane) plus the flux
+        // sum, rounded without bias
         T phn;
-        if constexpr (PHIP)   // phi plane: phi + flux sum, rounded without bias
-            phn = add_sr(ph, p.ga1 * sumL, sr_bits(p, gx, gy));
+        const uint32_t bits = PHIP ? sr_bits(p, gx, gy) : 0u;
+        if constexpr (PHIP)
+            phn = add_sr(KIND == KIND_T3B ? p.phi_acc[g] : ph, p.ga1 * sumL, bits);
         else
             phn = (KIND == KIND_T3B ? sumB : ph) + p.ga1 * sumL;
         {
@@ -562,12 +559,16 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             o1[0] = phn - r;
         }
         if constexpr (KIND == KIND_T3A) {
+            T ph2;
+            if constexpr (PHIP) ph2 = add_sr(ph, p.ga2 * sumL, mix32(bits));
+            else ph2 = ph + p.ga2 * sumL;
             T r = T(0);
 #pragma unroll
             for (int k = 1; k < 9; k++) r += o2[k];
-            o2[0] = (ph + p.ga2 * sumL) - r;
+            o2[0] = ph2 - r;
 #pragma unroll
             for (int k = 0; k < 9; k++) put_cell(p, p.out2 + k * plane, gx, gy, o2[k]);
+            if constexpr (PHIP) put_cell(p, p.phi_out2, gx, gy, ph2);
         }
         if constexpr (DEV) {
             __half *Oq = static_cast<__half *>(p.out1);

@@ -155,7 +155,8 @@ cudaError_t Launch<T, ST>::step_fast(const StepParams<T> &p, const FaceCoefs<T> 
 
 template <typename T, int ORDER, int FLUX, int KIND>
 static cudaError_t launch_fast3_t(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,
-                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, cudaStream_t s) {
+                                  const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc,
+                                  cudaStream_t s) {
     using FT = FastTile<T, T, 8, 2>;
     constexpr size_t smem = KIND == KIND_T3A ? FT::smem_bytes_t3a : FT::smem_bytes;
     auto kern = step_fast_kernel<T, T, ORDER, FLUX, 8, 2, KIND>;
@@ -171,16 +172,16 @@ static cudaError_t launch_fast3_t(const StepParams<T> &p, const FaceCoefs<T> &cf
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, p, cf, fe, tmX, tmPo, tmPo);
+    return cudaLaunchKernelEx(&cfg, kern, p, cf, fe, tmX, tmPo, tmPc);
 }
 
 template <typename T, typename ST>
 cudaError_t Launch<T, ST>::step_fast3(const StepParams<T> &p, const FaceCoefs<T> &cf, const FastExtra<T> &fe,
-                                      const CUtensorMap &tmX, const CUtensorMap &tmPo, int order, int flux, int kind,
-                                      cudaStream_t s) {
-#define DUGKS_T3(O, F)                                                                       \
-    return kind == KIND_T3A ? launch_fast3_t<T, O, F, KIND_T3A>(p, cf, fe, tmX, tmPo, s)      \
-                            : launch_fast3_t<T, O, F, KIND_T3B>(p, cf, fe, tmX, tmPo, s)
+                                      const CUtensorMap &tmX, const CUtensorMap &tmPo, const CUtensorMap &tmPc,
+                                      int order, int flux, int kind, cudaStream_t s) {
+#define DUGKS_T3(O, F)                                                                        \
+    return kind == KIND_T3A ? launch_fast3_t<T, O, F, KIND_T3A>(p, cf, fe, tmX, tmPo, tmPc, s) \
+                            : launch_fast3_t<T, O, F, KIND_T3B>(p, cf, fe, tmX, tmPo, tmPc, s)
     if (kind != KIND_T3A && kind != KIND_T3B) return cudaErrorInvalidValue;
     if (order == 2) {
         if (flux == 0) DUGKS_T3(2, 0);
