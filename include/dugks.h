@@ -61,7 +61,10 @@ enum { DUGKS_VEL_UNIFORM = 0, DUGKS_VEL_ROTATION = 1, DUGKS_VEL_VORTEX = 2, DUGK
  *              (Sec. II.B.2), which needs dt < 12 tau (Sec. III.A).
  *   precision  DUGKS_FP64, DUGKS_FP32, or DUGKS_FP16F (FP32 arithmetic; f stored
  *              in half precision as the scaled deviation f_k - w_k phi, phi kept
- *              in FP32; two-stage only).
+ *              in FP32; two-stage only). FP32 and FP16F keep phi as an FP32 plane
+ *              of its own and add each step's flux sum to it with unbiased
+ *              stochastic rounding (uniform bits hashed from cell and step, so
+ *              runs are deterministic); FP64 sums phi from the distribution.
  *   dtphiu     1 keeps the d(phi u)/dt term of the source Eq. (14b), evaluated
  *              by a backward difference over the last step; 0 drops it.
  *   phiA, phiB phase indicators (Eq. (3)), phiA != phiB; usually 1 and 0. */
