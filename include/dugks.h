@@ -113,6 +113,21 @@ int dugks_read_phi(dugks_ctx *c, double *out_host);
  * context's arithmetic type (double for FP64, float otherwise); no wait. */
 int dugks_read_phi_device(dugks_ctx *c, void *dev_out);
 
+/* Debug read-out of one step's face stage, for checking the path stage by
+ * stage (two-stage scheme). For the current state at t_n it writes, for every
+ * cell (x, y) and direction k (arrays of 9 * ny * nx doubles, index
+ * (k * ny + y) * nx + x, caller-owned):
+ *   fbar_E, fbar_N  bar f_k at the midpoint of the cell's east (x + 1) and north
+ *                   (y + 1) face at t_n + dt/2, reconstructed from bar f^+ at
+ *                   x_b - xi_k dt/2 (Eqs. (24)-(26), upwind or central);
+ *   f_E, f_N        the original distribution at those faces, Eqs. (27)-(28).
+ * The values come from the generic (plain) CUDA kernel in the context's
+ * arithmetic type, widened to double; the context's state, step index and mass
+ * do not change. Waits for the stream. DUGKS_EINVAL (not sticky) for a null
+ * output or a three-stage context; DUGKS_ENOMEM (not sticky) if the 36 * ny * nx
+ * doubles of device scratch cannot be allocated. */
+int dugks_debug_faces(dugks_ctx *c, double *fbar_E, double *fbar_N, double *f_E, double *f_N);
+
 /* Waits and returns the total mass sum phi over all cells, reduced in FP64 in
  * a fixed order (deterministic). DUGKS_ENONFINITE if it is NaN or Inf. */
 int dugks_mass(dugks_ctx *c, double *out);

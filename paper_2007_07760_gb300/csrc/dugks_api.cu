@@ -192,8 +192,11 @@ FastExtra<T> vortex_factors(const dugks_ctx *c, double t, double t_old, double t
 // One two-stage step, X[cur] -> X[1-cur]. phi as a sum of X (FP64): phi[pr0]
 // holds phi^{n-1}, phi[pr1] receives phi^n. phi as a plane of its own (FP32,
 // FP16F): phi[pr0] = phi^n (of X), phi[pr1] = phi^{n-1}, phi[pr2] receives phi^{n+1}.
+// dbg (debug read-out): the generic kernel evaluates the step of the current state,
+// writes its face values to dbg and its results only to scratch planes (the next
+// state set and phi plane, no mass partials); the context does not advance.
 template <typename T, typename ST>
-int step_t2(dugks_ctx *c) {
+int step_t2(dugks_ctx *c, double *dbg = nullptr) {
     StepParams<T> q = base_params<T>(c);
     const double dt = c->p.cfl, tau = 3.0 * c->p.M, h = 0.5 * dt;
     const double a = (2.0 * tau - h) / (2.0 * tau + dt), b = (dt + h) / (2.0 * tau + dt);
@@ -224,6 +227,12 @@ int step_t2(dugks_ctx *c) {
     q.phi_old = static_cast<const T *>(c->phi[iPo]);
     q.phi_out = static_cast<T *>(c->phi[iOut]);
     cudaError_t e;
+    if (dbg != nullptr) {
+        q.dbg = dbg;
+        q.mass_partial = nullptr;
+        e = Launch<T, ST>::step(q, c->p.order, c->p.flux, KIND_T2, c->stream);
+        return e == cudaSuccess ? DUGKS_OK : cuda_fail(c, e, "debug step kernel");
+    }
     if (c->fast && c->p.order == 4) {
         if (c->coef_h != h) {
             const FaceCoefs<T, 2> cf = make_face_coefs_r<T, 2>(4, c->p.flux, h);
@@ -680,6 +689,40 @@ int dugks_read_phi(dugks_ctx *c, double *out_host) {
     e = cudaMemcpyAsync(out_host, c->tmp, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "read phi");
     return sync_ctx(c);
+}
+
+int dugks_debug_faces(dugks_ctx *c, double *fbar_E, double *fbar_N, double *f_E, double *f_N) {
+    // (argument errors leave the context usable: they are not sticky)
+    if (!c || !fbar_E || !fbar_N || !f_E || !f_N) return DUGKS_EINVAL;
+    if (c->sticky != DUGKS_OK) return c->sticky;
+    if (c->p.stages != 2) {
+        c->err = "face read-out serves the two-stage scheme";
+        return DUGKS_EINVAL;
+    }
+    cudaSetDevice(c->dev);
+    int r = ensure_init(c);
+    if (r != DUGKS_OK) return r;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    double *d = nullptr;
+    if (cudaMalloc(&d, 4 * 9 * n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "face read-out buffer";
+        return DUGKS_ENOMEM;
+    }
+    switch (c->p.precision) {
+    case DUGKS_FP64: r = step_t2<double, double>(c, d); break;
+    case DUGKS_FP32: r = step_t2<float, float>(c, d); break;
+    default: r = step_t2<float, __half>(c, d); break;
+    }
+    double *outs[4] = {fbar_E, fbar_N, f_E, f_N};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 4 && r == DUGKS_OK && e == cudaSuccess; i++)
+        e = cudaMemcpyAsync(outs[i], d + (size_t)i * 9 * n, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (r == DUGKS_OK && e == cudaSuccess) r = sync_ctx(c);
+    else if (r == DUGKS_OK) r = cuda_fail(c, e, "face read-out copy");
+    cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    return r;
 }
 
 int dugks_mass_device(dugks_ctx *c, double *dev_out) {

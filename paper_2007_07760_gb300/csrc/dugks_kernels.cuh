@@ -104,6 +104,7 @@ struct StepParams {
     T t, t_old, t_face;         // time of X, of phi_old, of the faces
     T qscale, qinv;             // deviation storage scale s and 1 / s
     uint32_t seed;              // step index: the counter of the stochastic rounding
+    double *dbg;                // generic kernel, debug: face values out (null normally)
 };
 
 template <typename T>
@@ -506,6 +507,18 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             // c1 + c2 = 1: f_b = bar f + c2 (f^eq_b - bar f) + c3 S_b
             sFb[(2 * k) * NF + idx] = fe[k] + p.c2 * (feqE - fe[k]) + p.c3 * SE;
             sFb[(2 * k + 1) * NF + idx] = fn[k] + p.c2 * (feqN - fn[k]) + p.c3 * SN;
+        }
+        // debug read-out: bar f and f at the east and north faces of the tile's own
+        // cells, four arrays of 9 x ny x nx doubles (each face has one owner)
+        if (p.dbg != nullptr && fx >= 0 && fy >= 0 && x0 + fx < nx && y0 + fy < ny) {
+            const size_t n = (size_t)nx * ny, c = (size_t)gy * nx + gx;
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                p.dbg[(0 * 9 + k) * n + c] = (double)fe[k];
+                p.dbg[(1 * 9 + k) * n + c] = (double)fn[k];
+                p.dbg[(2 * 9 + k) * n + c] = (double)sFb[(2 * k) * NF + idx];
+                p.dbg[(3 * 9 + k) * n + c] = (double)sFb[(2 * k + 1) * NF + idx];
+            }
         }
     }
     __syncthreads();

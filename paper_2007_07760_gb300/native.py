@@ -48,6 +48,7 @@ SIGNATURES = [
     ("dugks_step", ctypes.c_int, [_VP, _I64]),
     ("dugks_read_phi", ctypes.c_int, [_VP, _DP]),
     ("dugks_read_phi_device", ctypes.c_int, [_VP, _VP]),
+    ("dugks_debug_faces", ctypes.c_int, [_VP, _DP, _DP, _DP, _DP]),
     ("dugks_mass", ctypes.c_int, [_VP, _DP]),
     ("dugks_mass_device", ctypes.c_int, [_VP, _VP]),
     ("dugks_status", ctypes.c_int, [_VP]),
@@ -142,6 +143,10 @@ def dugks_read_phi(ctx, out: np.ndarray):
 
 def dugks_read_phi_device(ctx, dev_ptr: int):
     _check(ctx, lib().dugks_read_phi_device(ctx, ctypes.c_void_p(dev_ptr)))
+
+
+def dugks_debug_faces(ctx, fbar_E: np.ndarray, fbar_N: np.ndarray, f_E: np.ndarray, f_N: np.ndarray):
+    _check(ctx, lib().dugks_debug_faces(ctx, _dptr(fbar_E), _dptr(fbar_N), _dptr(f_E), _dptr(f_N)))
 
 
 def dugks_mass(ctx) -> float:
@@ -395,6 +400,14 @@ class Solver:
 
     def mass(self) -> float:
         return dugks_mass(self.ctx)
+
+    def debug_faces(self):
+        """(bar f at east faces, at north faces, f at east faces, at north faces) of the
+        current state's step, each (9, ny, nx); the state does not advance."""
+        shape = (9, self.params.ny, self.params.nx)
+        out = [np.empty(shape) for _ in range(4)]
+        dugks_debug_faces(self.ctx, *out)
+        return tuple(out)
 
     @property
     def step_index(self) -> int:
