@@ -147,6 +147,15 @@ int dugks_status(dugks_ctx *c);
  * call on this context) reports DUGKS_ETIMEOUT. DUGKS_EINVAL for a bad count. */
 int dugks_selftest_wait_timeout(dugks_ctx *c, uint32_t max_polls);
 
+/* Self-test of the allocation-failure paths, on the host only (process-wide;
+ * the paper has no counterpart). After this call the next `skip` device
+ * allocations of the library proceed and the `count` after them report
+ * failure without asking the device; count = 0 disarms. An allocation that
+ * fails inside dugks_create frees what was allocated and returns DUGKS_ENOMEM;
+ * inside dugks_batch_add it returns DUGKS_ENOMEM and the batch stays usable.
+ * DUGKS_EINVAL for a negative argument. */
+int dugks_selftest_fail_allocs(int32_t skip, int32_t count);
+
 /* Text of the last error; never NULL (empty when there was none). */
 const char *dugks_last_error(const dugks_ctx *c);
 

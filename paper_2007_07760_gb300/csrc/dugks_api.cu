@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <atomic>
 #include <string>
 #include <utility>
 #include <vector>
@@ -463,6 +464,22 @@ int upload_plane(dugks_ctx *c, void *dst, const double *src) {
 }  // namespace
 
 namespace dugks {
+// allocation test hook: the next g_alloc_skip allocations proceed, the g_alloc_fail
+// after them fail
+static std::atomic<int> g_alloc_skip{0}, g_alloc_fail{0};
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes) {
+    if (g_alloc_fail.load(std::memory_order_relaxed) > 0) {
+        if (g_alloc_skip.fetch_sub(1, std::memory_order_relaxed) <= 0) {
+            g_alloc_skip.store(0, std::memory_order_relaxed);
+            g_alloc_fail.fetch_sub(1, std::memory_order_relaxed);
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 // Fixed-order sum of the per-tile partials (deterministic); flags NaN / Inf.
 // Thread t adds partials t, t + 256, ... in index order with 8 independent loads
 // in flight (one memory latency per 8 partials), then the fixed tree of block_sum.
@@ -561,13 +578,13 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     for (int s = 0; s < c->nsets && ok; s++) {
         // the three-stage accumulator (set 2) is always in the arithmetic type
         size_t es = (p->stages == 3) ? c->tsize : c->ssize;
-        ok = cudaMalloc(&c->X[s], 9 * c->plane * es) == cudaSuccess;
+        ok = dev_malloc(&c->X[s], 9 * c->plane * es) == cudaSuccess;
     }
-    for (int s = 0; s < c->nphi && ok; s++) ok = cudaMalloc(&c->phi[s], c->plane * c->tsize) == cudaSuccess;
-    if (ok) ok = cudaMalloc(&c->phi0, c->plane * c->tsize) == cudaSuccess;
-    if (ok) ok = cudaMalloc(&c->tmp, (size_t)p->nx * p->ny * sizeof(double)) == cudaSuccess;
-    if (ok) ok = cudaMalloc(&c->dmass, sizeof(double)) == cudaSuccess;
-    if (ok) ok = cudaMalloc(&c->dstatus, sizeof(int)) == cudaSuccess;
+    for (int s = 0; s < c->nphi && ok; s++) ok = dev_malloc(&c->phi[s], c->plane * c->tsize) == cudaSuccess;
+    if (ok) ok = dev_malloc(&c->phi0, c->plane * c->tsize) == cudaSuccess;
+    if (ok) ok = dev_malloc(&c->tmp, (size_t)p->nx * p->ny * sizeof(double)) == cudaSuccess;
+    if (ok) ok = dev_malloc(&c->dmass, sizeof(double)) == cudaSuccess;
+    if (ok) ok = dev_malloc(&c->dstatus, sizeof(int)) == cudaSuccess;
     if (ok && c->fast) {
         bool enc = p->precision == DUGKS_FP64 ? setup_fast<double, double>(c)
                    : p->precision == DUGKS_FP32 ? setup_fast<float, float>(c)
@@ -580,7 +597,7 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     }
     c->tiles_x = (p->nx + c->tile_w - 1) / c->tile_w;
     c->ntiles = c->tiles_x * ((p->ny + c->tile_h - 1) / c->tile_h);
-    if (ok) ok = cudaMalloc(&c->partial, (size_t)c->ntiles * sizeof(double)) == cudaSuccess;
+    if (ok) ok = dev_malloc(&c->partial, (size_t)c->ntiles * sizeof(double)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_ctx(c);
@@ -630,8 +647,8 @@ int dugks_set_velocity(dugks_ctx *c, int kind, const double *params, const doubl
                 return fail(c, DUGKS_EINVAL, "velocity field must be finite");
         cudaStreamSynchronize(c->stream);   // the field may be in use by queued steps
         if (!c->ufield) {
-            if (cudaMalloc(&c->ufield, c->plane * c->tsize) != cudaSuccess ||
-                cudaMalloc(&c->vfield, c->plane * c->tsize) != cudaSuccess) {
+            if (dev_malloc(&c->ufield, c->plane * c->tsize) != cudaSuccess ||
+                dev_malloc(&c->vfield, c->plane * c->tsize) != cudaSuccess) {
                 cudaGetLastError();
                 return fail(c, DUGKS_ENOMEM, "velocity field allocation");
             }
@@ -704,7 +721,7 @@ int dugks_debug_faces(dugks_ctx *c, double *fbar_E, double *fbar_N, double *f_E,
     if (r != DUGKS_OK) return r;
     const size_t n = (size_t)c->p.nx * c->p.ny;
     double *d = nullptr;
-    if (cudaMalloc(&d, 4 * 9 * n * sizeof(double)) != cudaSuccess) {
+    if (dev_malloc(&d, 4 * 9 * n * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         c->err = "face read-out buffer";
         return DUGKS_ENOMEM;
@@ -781,6 +798,14 @@ int dugks_selftest_wait_timeout(dugks_ctx *c, uint32_t max_polls) {
     return DUGKS_OK;
 }
 
+int dugks_selftest_fail_allocs(int32_t skip, int32_t count) {
+    if (skip < 0 || count < 0) return DUGKS_EINVAL;
+    dugks::g_alloc_fail.store(0, std::memory_order_relaxed);
+    dugks::g_alloc_skip.store(skip, std::memory_order_relaxed);
+    dugks::g_alloc_fail.store(count, std::memory_order_relaxed);
+    return DUGKS_OK;
+}
+
 int dugks_set_variant(dugks_ctx *c, int variant) {
     if (!c || variant < -1 || variant >= FAST_VARIANTS) return DUGKS_EINVAL;
     const bool fast_capable = (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) && encode_fn() != nullptr;
@@ -807,7 +832,7 @@ int dugks_set_variant(dugks_ctx *c, int variant) {
     if (ntiles > c->ntiles) {
         cudaFree(c->partial);
         c->partial = nullptr;
-        if (cudaMalloc(&c->partial, (size_t)ntiles * sizeof(double)) != cudaSuccess) {
+        if (dev_malloc(&c->partial, (size_t)ntiles * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, DUGKS_ENOMEM, "mass partials");
         }

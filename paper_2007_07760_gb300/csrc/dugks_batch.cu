@@ -156,8 +156,8 @@ int rebuild_t(dugks_batch *b) {
         const int cap = std::max(16, n * 2);
         void *grids = nullptr;
         double *mass = nullptr;
-        if (cudaMalloc(&grids, (size_t)cap * sizeof(BatchGrid<T>)) != cudaSuccess ||
-            cudaMalloc(&mass, (size_t)cap * sizeof(double)) != cudaSuccess) {
+        if (dev_malloc(&grids, (size_t)cap * sizeof(BatchGrid<T>)) != cudaSuccess ||
+            dev_malloc(&mass, (size_t)cap * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             if (grids) cudaFree(grids);
             return bfail(b, DUGKS_ENOMEM, "batch descriptors");
@@ -217,8 +217,8 @@ int rebuild_t(dugks_batch *b) {
         b->d_partials = nullptr;
         b->items_cap = 0;
         const int cap = b->nitems * 2;
-        if (cudaMalloc(&b->d_items, (size_t)cap * sizeof(int4)) != cudaSuccess ||
-            cudaMalloc(&b->d_partials, (size_t)cap * sizeof(double)) != cudaSuccess) {
+        if (dev_malloc(&b->d_items, (size_t)cap * sizeof(int4)) != cudaSuccess ||
+            dev_malloc(&b->d_partials, (size_t)cap * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return bfail(b, DUGKS_ENOMEM, "batch work list");
         }
@@ -288,7 +288,7 @@ StepParams<T> slot_view(const dugks_batch *b, const Slot &s) {
 template <typename T, typename ST>
 int init_slot(dugks_batch *b, Slot &s, const double *phi0) {
     void *d_phi0 = nullptr;
-    if (cudaMalloc(&d_phi0, s.plane * sizeof(T)) != cudaSuccess) {
+    if (dev_malloc(&d_phi0, s.plane * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         return DUGKS_ENOMEM;
     }
@@ -353,7 +353,7 @@ int dugks_batch_create(const dugks_params *common, void *cuda_stream, dugks_batc
         const int v = std::atoi(ev);
         if (v >= 0 && v < FAST_VARIANTS) b->variant = v;
     }
-    if (cudaMalloc(&b->d_status, sizeof(int)) != cudaSuccess) {
+    if (dev_malloc(&b->d_status, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         dugks_batch_destroy(b);
         return DUGKS_ENOMEM;
@@ -402,8 +402,8 @@ int dugks_batch_add(dugks_batch *b, int32_t nx, int32_t ny, const double *phi0_h
     for (int k = 0; k < nv; k++) s.vel[k] = vel_params[k];
     s.target = target_steps;
     bool ok = true;
-    for (int k = 0; k < 2 && ok; k++) ok = cudaMalloc(&s.X[k], 9 * s.plane * b->ssize) == cudaSuccess;
-    for (int k = 0; k < b->nphi && ok; k++) ok = cudaMalloc(&s.phi[k], s.plane * b->tsize) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; k++) ok = dev_malloc(&s.X[k], 9 * s.plane * b->ssize) == cudaSuccess;
+    for (int k = 0; k < b->nphi && ok; k++) ok = dev_malloc(&s.phi[k], s.plane * b->tsize) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_slot(s);
@@ -515,7 +515,7 @@ int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host) {
         if (b->d_tmp) cudaFree(b->d_tmp);
         b->d_tmp = nullptr;
         b->tmp_bytes = 0;
-        if (cudaMalloc(&b->d_tmp, bytes) != cudaSuccess) {
+        if (dev_malloc(&b->d_tmp, bytes) != cudaSuccess) {
             cudaGetLastError();
             return bfail(b, DUGKS_ENOMEM, "read-out buffer");
         }
@@ -552,7 +552,7 @@ int dugks_batch_mass(dugks_batch *b, int32_t grid_id, double *out) {
             if (b->d_tmp) cudaFree(b->d_tmp);
             b->d_tmp = nullptr;
             b->tmp_bytes = 0;
-            if (cudaMalloc(&b->d_tmp, need) != cudaSuccess) {
+            if (dev_malloc(&b->d_tmp, need) != cudaSuccess) {
                 cudaGetLastError();
                 return bfail(b, DUGKS_ENOMEM, "mass buffer");
             }

@@ -63,4 +63,13 @@ cudaError_t launch_batch_advance(BatchGrid<T> *grids, int ngrids, const double *
 
 cudaError_t launch_mass_final(const double *partial, int n, double *out, int *status, cudaStream_t s);
 
+// Every device allocation of the library goes through dev_malloc: cudaMalloc
+// behind a host-side test hook (dugks_selftest_fail_allocs) that can make chosen
+// allocations report cudaErrorMemoryAllocation without touching the device.
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+template <typename P>
+inline cudaError_t dev_malloc(P **p, size_t bytes) {
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 }  // namespace dugks

@@ -53,6 +53,7 @@ SIGNATURES = [
     ("dugks_mass_device", ctypes.c_int, [_VP, _VP]),
     ("dugks_status", ctypes.c_int, [_VP]),
     ("dugks_selftest_wait_timeout", ctypes.c_int, [_VP, ctypes.c_uint32]),
+    ("dugks_selftest_fail_allocs", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32]),
     ("dugks_last_error", ctypes.c_char_p, [_VP]),
     ("dugks_step_index", _I64, [_VP]),
     ("dugks_set_variant", ctypes.c_int, [_VP, ctypes.c_int]),
@@ -166,6 +167,11 @@ def dugks_status(ctx) -> int:
 def dugks_selftest_wait_timeout(ctx, max_polls: int) -> int:
     """Enqueues the bounded-wait self-test (see include/dugks.h); returns the code."""
     return lib().dugks_selftest_wait_timeout(ctx, int(max_polls))
+
+
+def dugks_selftest_fail_allocs(skip: int, count: int) -> int:
+    """Arms the host-side allocation-failure hook (see include/dugks.h); returns the code."""
+    return lib().dugks_selftest_fail_allocs(int(skip), int(count))
 
 
 def dugks_last_error(ctx) -> str:

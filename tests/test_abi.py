@@ -37,3 +37,11 @@ def test_params_struct_layout_matches_header():
     # int32 nx, ny; double W, M, cfl; int32 x5; (pad) double phiA, phiB
     assert native.dugks_params.phiB.offset + 8 == __import__("ctypes").sizeof(native.dugks_params)
     assert native.dugks_params.W.offset == 8 and native.dugks_params.order.offset == 32
+
+
+def test_allocation_hook_arguments():
+    # host-only entry point: argument checks, arming and disarming
+    assert native.dugks_selftest_fail_allocs(-1, 1) == native.DUGKS_EINVAL
+    assert native.dugks_selftest_fail_allocs(0, -1) == native.DUGKS_EINVAL
+    assert native.dugks_selftest_fail_allocs(3, 1) == native.DUGKS_OK
+    assert native.dugks_selftest_fail_allocs(0, 0) == native.DUGKS_OK
