@@ -12,6 +12,12 @@ step target. At every slice boundary the server
 * collects the grids that reached their target (phi copied back, slot freed),
 * launches the next slice.
 
+A request whose grid cannot be added fails alone: a non-finite initial field
+(DUGKS_ENONFINITE) or any other refusal is recorded as that request's result,
+with its status code, and the others go on; DUGKS_ENOMEM is transient, so the
+request goes back to the head of the queue until running grids finish (it
+fails only when nothing else holds memory).
+
 Time-to-result = completion time - arrival time (queueing included). A grid's
 result does not depend on what else is in the batch (bitwise; see the tests).
 The backend is any object with the Batch interface, so the policy runs on the
@@ -27,6 +33,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import workloads as WL
+from .native import DUGKS_ENOMEM
 
 
 @dataclass
@@ -36,6 +43,7 @@ class Request:
     n: int                  # grid side (n x n cells)
     steps: int
     kind: str               # "rotation" (slotted disk) or "vortex" (single vortex)
+    phi0: np.ndarray | None = field(default=None, repr=False)   # caller's field (else synthetic)
 
     @property
     def cells(self) -> int:
@@ -51,6 +59,7 @@ class Result:
     admitted: float
     finished: float
     phi: np.ndarray | None = field(default=None, repr=False)
+    error: int = 0          # status code of a request that failed (0: solved)
 
     @property
     def latency(self) -> float:
@@ -80,12 +89,15 @@ def request_field(req: Request, cfl: float = 0.8, W: float = 4.0, umax: float = 
     steps unless that would exceed the peak speed umax at the box corners (the
     scheme needs |u| well below the lattice speed); then it turns more slowly."""
     n = req.n
+    phi0 = req.phi0   # the caller's field, with the kind's velocity; else the synthetic one
     if req.kind == "rotation":
         s = n / 256.0
-        phi0 = WL.slotted_disk(n, 128 * s, 160 * s, 64 * s, 16 * s, 80 * s, W)
+        if phi0 is None:
+            phi0 = WL.slotted_disk(n, 128 * s, 160 * s, 64 * s, 16 * s, 80 * s, W)
         omega = min(2.0 * math.pi / (req.steps * cfl), umax * math.sqrt(2.0) / n)
         return phi0, "rotation", (n / 2, n / 2, omega)
-    phi0 = WL.drops(n, n, [(0.5 * n, 0.75 * n)], [0.15 * n], W)
+    if phi0 is None:
+        phi0 = WL.drops(n, n, [(0.5 * n, 0.75 * n)], [0.15 * n], W)
     return phi0, "vortex", (float(n), umax, req.steps * cfl)
 
 
@@ -133,7 +145,17 @@ class Server:
                 break
             queue.popleft()
             phi0, kind, vel = request_field(req, self.cfl, self.W)
-            gid = self.b.add(phi0, kind, vel, req.steps)
+            try:
+                gid = self.b.add(phi0, kind, vel, req.steps)
+            except Exception as e:   # the backend's error carries the status code
+                code = getattr(e, "code", None)
+                if code is None:
+                    raise
+                if code == DUGKS_ENOMEM and (self.active or self.resident):
+                    queue.appendleft(req)   # transient: retry once running grids free memory
+                    break
+                self.results.append(Result(req.rid, req.n, req.steps, req.arrival, now, now, None, int(code)))
+                continue
             self.used += nbytes
             self.peak_used = max(self.peak_used, self.used)
             self.active[gid] = (req, now, nbytes)
@@ -152,7 +174,7 @@ class Server:
     def run(self, trace: list[Request], time_scale: float = 1.0, max_wall: float | None = None) -> dict:
         """Replays `trace` (arrival times divided by time_scale) until every request
         has finished. Returns throughput and latency statistics."""
-        pending = deque(sorted((Request(r.rid, r.arrival / time_scale, r.n, r.steps, r.kind) for r in trace),
+        pending = deque(sorted((Request(r.rid, r.arrival / time_scale, r.n, r.steps, r.kind, r.phi0) for r in trace),
                                key=lambda r: r.arrival))
         queue: deque = deque()
         self.t0 = self.clock()
@@ -179,9 +201,10 @@ class Server:
             self._collect()
         wall = self.clock() - self.t0
         status = self.b.status() if hasattr(self.b, "status") else 0
-        lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
-        return {"requests": len(self.results), "wall_s": wall, "slices": slices,
-                "solves_per_s": len(self.results) / wall if wall > 0 else 0.0,
+        solved = [r for r in self.results if r.error == 0]
+        lat = np.array([r.latency for r in solved]) if solved else np.zeros(1)
+        return {"requests": len(self.results), "failed": len(self.results) - len(solved), "wall_s": wall,
+                "slices": slices, "solves_per_s": len(solved) / wall if wall > 0 else 0.0,
                 "cell_updates_per_s": self.cell_updates / wall if wall > 0 else 0.0,
                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "mean_s": float(lat.mean()), "peak_bytes": self.peak_used, "budget_bytes": self.budget,

@@ -104,6 +104,95 @@ def test_request_larger_than_budget_rejected():
         srv.run(small_trace(count=2))
 
 
+class CodedError(RuntimeError):
+    """Stand-in for the binding's error: carries a status code."""
+
+    def __init__(self, code):
+        super().__init__(f"status {code}")
+        self.code = code
+
+
+class RefusingBatch(FakeBatch):
+    """FakeBatch whose add refuses a non-finite field (ENONFINITE) and reports
+    ENOMEM on the add calls listed in `enomem_calls` (0-based)."""
+
+    def __init__(self, clock, enomem_calls=()):
+        super().__init__(clock)
+        self.calls = 0
+        self.enomem_calls = set(enomem_calls)
+
+    def add(self, phi0, kind, vel, target):
+        call = self.calls
+        self.calls += 1
+        if not np.isfinite(phi0).all():
+            raise CodedError(5)
+        if call in self.enomem_calls:
+            raise CodedError(2)
+        return super().add(phi0, kind, vel, target)
+
+
+def _with_nan(trace, rid):
+    out = []
+    for r in trace:
+        if r.rid == rid:
+            phi0, _, _ = S.request_field(r)
+            phi0 = phi0.copy()
+            phi0[1, 2] = np.nan
+            r = S.Request(r.rid, r.arrival, r.n, r.steps, r.kind, phi0)
+        out.append(r)
+    return out
+
+
+def test_non_finite_request_fails_alone():
+    clock = FakeClock()
+    srv = S.Server(RefusingBatch(clock), budget_bytes=3 * 256 * 256 * 80, max_slots=8, slice_steps=16,
+                   clock=clock, sleep=clock.sleep)
+    trace = _with_nan(small_trace(count=12), rid=5)
+    st = srv.run(trace)
+    res = {r.rid: r for r in srv.results}
+    assert st["requests"] == 12 and st["failed"] == 1
+    assert res[5].error == 5 and res[5].phi is None
+    assert all(res[r.rid].error == 0 and res[r.rid].finished >= r.arrival for r in trace if r.rid != 5)
+
+
+def test_out_of_memory_is_retried_then_fails_only_when_alone():
+    clock = FakeClock()
+    fb = RefusingBatch(clock, enomem_calls=(2, 3))
+    srv = S.Server(fb, budget_bytes=3 * 256 * 256 * 80, max_slots=8, slice_steps=16, clock=clock, sleep=clock.sleep)
+    trace = small_trace(count=12, rate=1e7)   # all queued at once: two grids run when the third is refused
+    st = srv.run(trace)
+    assert fb.calls == 14                                  # the refused request was tried three times
+    assert st["failed"] == 0 and st["requests"] == 12   # retried once running grids finished
+    adm = [r.admitted for r in sorted(srv.results, key=lambda r: r.rid)]
+    assert all(a <= b + 1e-12 for a, b in zip(adm, adm[1:]))   # still first come, first served
+    clock = FakeClock()
+    srv = S.Server(RefusingBatch(clock, enomem_calls=(0,)), budget_bytes=3 * 256 * 256 * 80, clock=clock,
+                   sleep=clock.sleep)
+    st = srv.run(small_trace(count=3))
+    assert st["failed"] == 1 and srv.results[0].error == 2   # nothing running to wait for
+
+
+@pytest.mark.gpu
+def test_served_non_finite_request_fails_alone():
+    from paper_2007_07760_gb300 import native as N
+    common = dict(W=4.0, M=0.02, cfl=0.8, order=3, flux=0, stages=2, precision="fp32")
+    trace = _with_nan(S.poisson_trace(6, rate=2000.0, seed=9, nmin=32, nmax=64, smin=20, smax=60), rid=2)
+    with N.Batch(**common) as b:
+        srv = S.Server(b, budget_bytes=3 * b.grid_bytes(64, 64), slice_steps=8, keep_fields=True)
+        st = srv.run(trace)
+        assert st["status"] == 0 and b.status() == 0
+    res = {r.rid: r for r in srv.results}
+    assert st["failed"] == 1 and res[2].error == N.DUGKS_ENONFINITE
+    for req in trace:
+        if req.rid == 2:
+            continue
+        phi0, kind, vel = S.request_field(req)
+        with N.Batch(**common) as solo:
+            g = solo.add(phi0, kind, vel, req.steps)
+            solo.step(req.steps)
+            assert np.array_equal(solo.phi(g), res[req.rid].phi)
+
+
 @pytest.mark.gpu
 def test_served_results_equal_solo_runs():
     from paper_2007_07760_gb300 import native as N
