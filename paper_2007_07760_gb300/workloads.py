@@ -2,7 +2,8 @@
 
 This module only builds initial order-parameter fields and velocity-field
 parameters (Sec. III: translation of a circular interface, Zalesak's slotted disk
-under rigid rotation, a reversing vortex). It contains none of the DUGKS
+under rigid rotation, the extension of a circle in a reversed shear flow, a
+reversing vortex). It contains none of the DUGKS
 arithmetic and is the one module both the CUDA path's callers and the oracle's
 tests draw their inputs from.
 
@@ -140,6 +141,19 @@ def random_batch(count: int = 512, seed: int = SEED_BASE + 3, nmin: int = 64, nm
         out.append(Problem(f"batch{g}", n, n, 4.0, 0.02, cfl, order, 0, 2, "uniform",
                            (sp * math.cos(ang), sp * math.sin(ang)), phi0, steps))
     return out
+
+
+def extension(Pe: float, cfl: float, L0: int = 256, M: float = 0.02, W: float = 4.0):
+    """Interface extension in a shear flow (Sec. III.C): circle R = L0/5 centred at
+    (0.5 L0, 0.3 L0), cell-centre velocity u = U0 pi sin(pi x/L0) cos(pi y/L0),
+    v = -U0 pi cos(pi x/L0) sin(pi y/L0) with U0 = Pe M / L0, reversed after
+    T_f = L0/U0 and run for another T_f. Returns (phi0, u, v, steps per half)."""
+    U0 = Pe * M / L0
+    X, Y = centres(L0, L0)
+    u = U0 * math.pi * np.sin(math.pi * X / L0) * np.cos(math.pi * Y / L0)
+    v = -U0 * math.pi * np.cos(math.pi * X / L0) * np.sin(math.pi * Y / L0)
+    phi0 = drops(L0, L0, [(0.5 * L0, 0.3 * L0)], [L0 / 5], W)
+    return phi0, u, v, int(round(L0 / U0 / cfl))
 
 
 def translation(n: int, order: int, flux: int, stages: int, cfl: float,
