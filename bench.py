@@ -41,6 +41,13 @@ from paper_2007_07760_gb300 import workloads as WL  # noqa: E402
 METRIC = "D2Q9 cell-updates/s"
 UNIT = "cell-updates/s"
 BYTES_PER_CELL = {"fp64": 160, "fp32": 84, "fp16f": 48}   # two-stage, with d(phi u)/dt
+# three-stage: the two kernels of a step move 57 planes between them (FP64), 62 with
+# the FP32 phi planes
+BYTES_PER_CELL_T3 = {"fp64": 456, "fp32": 248}
+
+
+def bytes_per_cell(precision: str, stages: int) -> int:
+    return BYTES_PER_CELL[precision] if stages == 2 else BYTES_PER_CELL_T3[precision]
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes) of one step
@@ -281,8 +288,7 @@ def also_single(name: str, precision: str, K: int, generic: bool = False):
             solver.set_variant(-1)
         r = time_single(solver, stream, 10, K)
     peak, _ = measured_peak_hbm()
-    # the three-stage scheme runs two kernels per step, which move 56 values per cell between them
-    bpc = BYTES_PER_CELL[precision] if prob.stages == 2 else {"fp64": 456, "fp32": 248}[precision]
+    bpc = bytes_per_cell(precision, prob.stages)
     achieved = bpc * prob.cells / (r["avg_step_ms"] * 1e-3) / 1e9
     return {"workload": desc["workload"] + ("_generic_kernel" if generic else ""), "bytes_per_cell": bpc,
             "value": prob.cells * K / (r["total_ms"] * 1e-3), "unit": UNIT, "steps": K,
@@ -338,7 +344,8 @@ def run_ours(args):
 
     value = job_rate(prob.cells * K, world, total_ms * 1e-3)
     peak, peak_kind = measured_peak_hbm()
-    achieved = BYTES_PER_CELL[args.precision] * prob.cells / (avg_step_ms * 1e-3) / 1e9
+    bpc = bytes_per_cell(args.precision, prob.stages)
+    achieved = bpc * prob.cells / (avg_step_ms * 1e-3) / 1e9
     sha = kernel_source_hash()
     traffic = NCU_TRAFFIC.get((sha, desc["workload"]))
 
@@ -379,8 +386,10 @@ def run_ours(args):
                            replicas=world, parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": desc.get("kernel", "step_fast_kernel (TMA-staged fused two-stage DUGKS step)"),
-                         "bytes_per_cell": BYTES_PER_CELL[args.precision], "peak_source": peak_kind,
+                         "kernel": desc.get("kernel", "step_fast_kernel (TMA-staged fused two-stage DUGKS step)"
+                                            if prob.stages == 2 else
+                                            "step_fast_kernel KIND_T3A + KIND_T3B (the two kernels of a three-stage step)"),
+                         "bytes_per_cell": bpc, "peak_source": peak_kind,
                          "avg_kernel_ms": avg_step_ms},
             "e2e": e2e,
             "gpu_launches": launches_per_step * K,
