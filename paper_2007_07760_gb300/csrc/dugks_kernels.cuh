@@ -82,7 +82,7 @@ struct StepParams {
     int tile_w, tile_h;         // cells per CTA tile (mass partial kernel)
     const void *X;              // 9 planes in (storage type)
     const void *acc;            // KIND_T3B: accumulator planes (type T)
-    const T *phi_cur;           // deviation storage: phi of X (authoritative)
+    const T *phi_cur;           // phi plane: phi of X (authoritative)
     const T *phi_old;           // phi at the older time level of d(phi u)/dt
     T *phi_out;                 // phi plane: phi of out1; otherwise (T2/T3A) phi of X
     T *phi_out2;                // phi plane, T3A: phi of out2 (the accumulator)
