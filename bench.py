@@ -56,7 +56,7 @@ L2_FLUSH_BYTES = 512 << 20
 # writes of a 1024^2 step stay in L2 (129 MB) during the launch and reach DRAM
 # later, so the figure is the read traffic plus the evictions.
 NCU_TRAFFIC = {
-    ("9dff706a5e2f5739", "vortex1024_fp32_p3_upwind_2stage"): 51128064,
+    ("275d00dd7c95291c", "vortex1024_fp32_p3_upwind_2stage"): 51128064,
 }
 
 

@@ -5,7 +5,9 @@
 //  * the tile's 9 distribution planes plus a halo of 1 + 2R cells (stencil radius
 //    R = 1 for orders 2-3, 2 for order 4) arrive in shared memory as ONE 3D TMA
 //    box (the ghost border of the plane layout makes every halo a plain
-//    rectangle), the older phi plane as a 2D box; one mbarrier, bounded wait;
+//    rectangle), the older phi plane as a 2D box (and, where phi is a plane of its
+//    own -- FP32, FP16 storage -- phi of the state as a second one); one mbarrier,
+//    bounded wait;
 //  * the loop over the 9 velocities is outermost and unrolled (lattice constants,
 //    stencil coefficients and the stencils' structural zeros are compile-time per
 //    direction): per direction k, bar f^+_k on the tile + R + 1 cells, then bar
@@ -19,7 +21,8 @@
 //    During the direction loop each cell's X_k + beta (g_k - X_k) + gamma L_k
 //    minus its phi_b part is written over X_k in the TMA buffer (dead by then);
 //    once phi_b is known, a second loop adds the phi_b part (in closed form over
-//    k) and stores.
+//    k) and stores; a phi plane receives phi + the flux sum, stochastically
+//    rounded (add_sr).
 // Thread layout: a warp owns 32 consecutive face-owner columns (lane l is column
 // l - 1) and MR consecutive rows; the CTA's face owners are 32 x (NW * MR), its
 // cells TX = 31 by TY = NW * MR - 1.
