@@ -98,11 +98,13 @@ int dugks_set_velocity(dugks_ctx *c, int kind, const double *params, const doubl
                        const double *v_host);
 
 /* Enqueues nsteps >= 0 full time steps on the context's stream and returns
- * without waiting. Two-stage: one fused kernel per step (stages a1-a5 of the
- * method: cell moments and bar f^+ with source, isotropic gradients, face
- * reconstruction at x_b - xi h, face phi / f^eq / source / original f,
- * meso-flux update), which also writes per-tile FP64 mass partials.
- * Three-stage: two kernels per step (steps (i)-(ii) and (iii)-(iv)). */
+ * without waiting. Two-stage (Sec. II.B.2, the original DUGKS): one fused
+ * kernel per step, which computes the cell moments, the source of Eq. (14b)
+ * and bar f^+, the isotropic gradients of Eq. (2) and of the reconstruction,
+ * bar f at x_b - xi h by Eqs. (24)-(26), the face phi, equilibrium, source
+ * and original f of Eqs. (27)-(28), and the meso-flux update of Eq. (21), and
+ * also writes per-tile FP64 mass partials. Three-stage (Eqs. (29)-(34)): two
+ * kernels per step (steps (i)-(ii) and (iii)-(iv) of Sec. II.B.2). */
 int dugks_step(dugks_ctx *c, int64_t nsteps);
 
 /* Waits for the stream and writes phi = sum_k f_k (Eq. (30)) into out_host
@@ -241,23 +243,26 @@ const char *dugks_batch_last_error(const dugks_batch *b);
 void dugks_batch_destroy(dugks_batch *b);
 
 /* Allocation-free FP64 sum of a device field. The paper has no counterpart:
- * this exists for callers that cannot call cudaMalloc where they need a mass,
- * such as code running while a stream is captured into a CUDA graph, hosts
- * whose device memory is fully reserved by another allocator, and latency-
- * critical loops that cannot take the implicit synchronisation of cudaMalloc.
- * It runs the same reduction as dugks_mass_device (one FP64 partial per 32 x 8
- * tile, then a fixed-order sum) with the partials in a static device array of
- * DUGKS_NOALLOC_MAX_TILES doubles (512 KiB), which every GPU that loads the
- * library holds until the process exits.
+ * this exists for callers that cannot call cudaMalloc where they need a mass:
+ * hosts whose device memory is fully reserved by another allocator (a
+ * framework's caching pool hands out no raw cudaMalloc memory), and
+ * latency-critical loops that cannot take the implicit device synchronisation
+ * of cudaMalloc and cudaFree. It runs the same reduction as dugks_mass_device
+ * (one FP64 partial per 32 x 8 tile, then a fixed-order sum) with the partials
+ * in a static device array of DUGKS_NOALLOC_MAX_TILES doubles (512 KiB), which
+ * every GPU that loads the library holds until the process exits. It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  *   field    device pointer: ny rows of nx values, row stride pitch elements
  *   dtype    0 = double, 1 = float
  *   out_dev  device pointer to one double, written by the kernels
  *   cuda_stream  cudaStream_t to launch on (NULL = legacy default stream)
  * Returns DUGKS_EINVAL for bad arguments or when ceil(nx/32) * ceil(ny/8)
- * exceeds DUGKS_NOALLOC_MAX_TILES (e.g. more than 4096 x 4096 cells), and
- * DUGKS_ECUDA when the launch fails. It enqueues work and does not wait.
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * exceeds DUGKS_NOALLOC_MAX_TILES (e.g. more than 4096 x 4096 cells; any shape
+ * within the limit is served, down to one tile column of 524288 rows), and
+ * DUGKS_ECUDA when one of its own launches fails (an error left pending by
+ * earlier work is neither reported nor cleared). It enqueues work and does not
+ * wait. The first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream capture.
  * Every call on a device shares the array: calls whose kernels may overlap on
  * the GPU (different streams without ordering) race and must be serialised by
  * the caller. Each call overwrites the entries it reads, so no clearing is

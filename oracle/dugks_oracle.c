@@ -19,7 +19,10 @@
  * Parity pins: stencils by polynomial exactness and measured order; face values
  * by an independent brute-force routine; the step by mass conservation, uniform
  * invariance, the stationary tanh slab, and the closed-form decay and drift of a
- * Fourier mode under advection-diffusion (theta = 0).
+ * Fourier mode under advection-diffusion (theta = 0); the velocity fields by
+ * their stream functions, and the time levels at which the step evaluates them
+ * by a mode that a reversing flow must return to its start (test-only velocity
+ * kind 4).
  */
 #include "dugks_oracle.h"
 
@@ -243,6 +246,12 @@ void orc_velocity(const orc_params *p, double x, double y, double t, double uv[2
         uv[1] = (1 - fx) * (1 - fy) * v00 + fx * (1 - fy) * v10 + (1 - fx) * fy * v01 + fx * fy * v11;
         return;
     }
+    case 4: { /* uniform flow reversed by the vortex's factor cos(pi t / T): test-only kind
+               * whose exact displacement (ux, uy) T / pi sin(pi t / T) pins the time levels */
+        double c = cos(PI * t / p->vel[2]);
+        uv[0] = p->vel[0] * c; uv[1] = p->vel[1] * c;
+        return;
+    }
     default:
         uv[0] = uv[1] = 0.0;
     }
@@ -435,9 +444,10 @@ int orc_check(const orc_params *p) {
     if (p->order < 2 || p->order > 4 || (p->flux != 0 && p->flux != 1)) return -1;
     if (p->stages != 2 && p->stages != 3) return -1;
     if (p->phiA == p->phiB) return -1;
-    if (p->vel_kind < 0 || p->vel_kind > 3) return -1;
+    if (p->vel_kind < 0 || p->vel_kind > 4) return -1;
     if (p->vel_kind == 3 && (!p->u_field || !p->v_field)) return -1;
     if (p->vel_kind == 2 && (p->vel[0] <= 0 || p->vel[2] <= 0)) return -1;
+    if (p->vel_kind == 4 && !(p->vel[2] > 0)) return -1;
     /* Three-stage DUGKS needs dt < 12 tau (Sec. III.A). */
     if (p->stages == 3 && !(p->cfl < 12.0 * p->M / RT)) return -1;
     return 0;

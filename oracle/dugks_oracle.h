@@ -31,8 +31,10 @@ typedef struct {
     int stages;      /* 2 = original DUGKS, 3 = three-stage third-order DUGKS */
     int dtphiu;      /* 1 = keep the d(phi u)/dt part of the source Eq. (14b) */
     double phiA, phiB;
-    int vel_kind;    /* 0 uniform, 1 rigid rotation, 2 single vortex, 3 cell field */
-    double vel[4];   /* uniform (ux, uy); rotation (cx, cy, omega); vortex (L, U, T) */
+    int vel_kind;    /* 0 uniform, 1 rigid rotation, 2 single vortex, 3 cell field,
+                        4 reversing uniform (test-only: pins the time levels) */
+    double vel[4];   /* uniform (ux, uy); rotation (cx, cy, omega); vortex (L, U, T);
+                        reversing uniform (ux, uy, T): (ux, uy) cos(pi t / T) */
     const double *u_field, *v_field;   /* vel_kind 3: cell-centre components */
 } orc_params;
 

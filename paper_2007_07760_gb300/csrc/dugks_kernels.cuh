@@ -304,7 +304,9 @@ __device__ __forceinline__ double block_sum(double v, double *sred) {
 }
 
 // 32-bit integer hash (xor-shift / multiply rounds), used as a counter-based
-// source of uniform bits: hash(cell, step) needs no state
+// source of uniform bits: hash(cell, step) needs no state. Shifts and
+// multipliers are the published "lowbias32" constants found by C. Wellons'
+// hash-prospector search ("Prospecting for Hash Functions", 2018).
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352du;

@@ -2,14 +2,13 @@
 //
 // The context API keeps its per-tile mass partials in memory it allocates
 // with cudaMalloc. Some callers cannot allocate at the point where they need a
-// mass: code that runs while a stream is being captured into a CUDA graph
-// (cudaMalloc is not a stream operation and may be refused there), hosts whose
-// device memory is entirely reserved by another allocator (a framework's
-// caching pool), and latency-critical loops that must not take the implicit
-// device synchronisation of cudaMalloc / cudaFree. For them this file provides
-// the same two-kernel reduction (one FP64 partial per 32 x 8 tile, then one
-// CTA summing the partials in a fixed order) with the partials in a
-// file-scope device array instead.
+// mass: hosts whose device memory is entirely reserved by another allocator (a
+// framework's caching pool, which hands out no raw cudaMalloc memory), and
+// latency-critical loops that must not take the implicit device
+// synchronisation of cudaMalloc / cudaFree. For them this file provides the
+// same two-kernel reduction (one FP64 partial per 32 x 8 tile, then one CTA
+// summing the partials in a fixed order) with the partials in a file-scope
+// device array instead.
 //
 // The array is static device memory of this library: every GPU on which the
 // library's kernels are loaded holds it (512 KiB) until the process exits.
@@ -32,7 +31,10 @@ template <typename T>
 __global__ void __launch_bounds__(256)
 field_partial_kernel(const T *field, int nx, int ny, int pitch, int tiles_x, double *partial) {
     __shared__ double sred[32];
-    const int x0 = blockIdx.x * NOALLOC_TILE_X, y0 = blockIdx.y * NOALLOC_TILE_Y;
+    // one-dimensional grid of tiles (tile = by * tiles_x + bx): a field one tile
+    // wide may have up to NOALLOC_MAX_TILES tile rows, beyond the y-grid limit
+    const int tile = blockIdx.x, by = tile / tiles_x, bx = tile - by * tiles_x;
+    const int x0 = bx * NOALLOC_TILE_X, y0 = by * NOALLOC_TILE_Y;
     double msum = 0.0;
     for (int idx = threadIdx.x; idx < NOALLOC_TILE_X * NOALLOC_TILE_Y; idx += blockDim.x) {
         const int ly = idx / NOALLOC_TILE_X, lx = idx - ly * NOALLOC_TILE_X;
@@ -41,7 +43,7 @@ field_partial_kernel(const T *field, int nx, int ny, int pitch, int tiles_x, dou
         msum += (double)field[(size_t)gy * pitch + gx];
     }
     const double s = dugks::block_sum(msum, sred);
-    if (threadIdx.x == 0) partial[blockIdx.y * tiles_x + blockIdx.x] = s;
+    if (threadIdx.x == 0) partial[tile] = s;
 }
 
 __global__ void __launch_bounds__(256) field_final_kernel(const double *partial, int n, double *out) {
@@ -86,13 +88,18 @@ extern "C" int dugks_field_mass_noalloc(const void *field, int dtype, int32_t nx
     int r = scratch_for_current_device(&scratch);
     if (r != DUGKS_OK) return r;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    dim3 grid(tiles_x, (ny + NOALLOC_TILE_Y - 1) / NOALLOC_TILE_Y);
-    if (dtype == 0)
-        field_partial_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double *>(field), nx, ny, pitch, tiles_x,
-                                                          scratch);
-    else
-        field_partial_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float *>(field), nx, ny, pitch, tiles_x,
-                                                         scratch);
-    field_final_kernel<<<1, 256, 0, s>>>(scratch, (int)tiles, out_dev);
-    return cudaGetLastError() == cudaSuccess ? DUGKS_OK : DUGKS_ECUDA;
+    // launched through cudaLaunchKernel so that each launch's own status is
+    // returned (an earlier, unrelated error pending on this thread is neither
+    // reported as this call's failure nor cleared)
+    const void *field_arg = field;
+    int ntiles = (int)tiles, nx_ = nx, ny_ = ny, pitch_ = pitch, tx_ = tiles_x;
+    void *pargs[] = {&field_arg, &nx_, &ny_, &pitch_, &tx_, &scratch};
+    const void *pk = dtype == 0 ? reinterpret_cast<const void *>(&field_partial_kernel<double>)
+                                : reinterpret_cast<const void *>(&field_partial_kernel<float>);
+    if (cudaLaunchKernel(pk, dim3(ntiles), dim3(256), pargs, 0, s) != cudaSuccess) return DUGKS_ECUDA;
+    void *fargs[] = {&scratch, &ntiles, &out_dev};
+    if (cudaLaunchKernel(reinterpret_cast<const void *>(&field_final_kernel), dim3(1), dim3(256), fargs, 0, s) !=
+        cudaSuccess)
+        return DUGKS_ECUDA;
+    return DUGKS_OK;
 }

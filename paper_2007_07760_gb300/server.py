@@ -14,9 +14,11 @@ step target. At every slice boundary the server
 
 A request whose grid cannot be added fails alone: a non-finite initial field
 (DUGKS_ENONFINITE) or any other refusal is recorded as that request's result,
-with its status code, and the others go on; DUGKS_ENOMEM is transient, so the
-request goes back to the head of the queue until running grids finish (it
-fails only when nothing else holds memory).
+with its status code, and the others go on; DUGKS_ENOMEM is transient while
+grids that will finish hold memory, so the request goes back to the head of
+the queue until they do; with nothing running but resident grids (which never
+finish) it fails at once, as does a request that fits the budget only without
+the resident grids.
 
 Time-to-result = completion time - arrival time (queueing included). A grid's
 result does not depend on what else is in the batch (bitwise; see the tests).
@@ -142,7 +144,12 @@ class Server:
             if nbytes > self.budget:
                 raise ValueError(f"request {req.rid} can never fit the budget")
             if self.used + nbytes > self.budget:
-                break
+                if self.active:
+                    break   # waits for running grids to free memory
+                # only resident grids hold memory and they never finish: it can never fit
+                queue.popleft()
+                self.results.append(Result(req.rid, req.n, req.steps, req.arrival, now, now, None, DUGKS_ENOMEM))
+                continue
             queue.popleft()
             phi0, kind, vel = request_field(req, self.cfl, self.W)
             try:
@@ -151,8 +158,10 @@ class Server:
                 code = getattr(e, "code", None)
                 if code is None:
                     raise
-                if code == DUGKS_ENOMEM and (self.active or self.resident):
-                    queue.appendleft(req)   # transient: retry once running grids free memory
+                if code == DUGKS_ENOMEM and self.active:
+                    # transient while grids that will finish hold memory: retry once they have
+                    # (resident grids never finish, so with only those it fails now)
+                    queue.appendleft(req)
                     break
                 self.results.append(Result(req.rid, req.n, req.steps, req.arrival, now, now, None, int(code)))
                 continue

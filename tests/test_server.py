@@ -172,6 +172,28 @@ def test_out_of_memory_is_retried_then_fails_only_when_alone():
     assert st["failed"] == 1 and srv.results[0].error == 2   # nothing running to wait for
 
 
+def test_out_of_memory_beside_resident_grids_fails_and_ends():
+    # a resident grid never finishes: ENOMEM with only residents on the device, or a
+    # request that fits the budget only without them, must fail the request, not spin
+    clock = FakeClock()
+    fb = RefusingBatch(clock, enomem_calls=(1,))   # call 0 adds the resident grid
+    srv = S.Server(fb, budget_bytes=3 * 256 * 256 * 80, slice_steps=16, clock=clock, sleep=clock.sleep)
+    srv.add_resident(np.zeros((64, 64)), "vortex", (64.0, 0.05, 100.0))
+    trace = small_trace(count=3)
+    st = srv.run(trace, max_wall=1e3)
+    assert st["requests"] == 3 and st["failed"] == 1
+    first = min(trace, key=lambda r: r.arrival).rid
+    assert {r.rid: r for r in srv.results}[first].error == 2
+    clock = FakeClock()
+    srv = S.Server(FakeBatch(clock), budget_bytes=300 * 300 * 80, slice_steps=16, clock=clock, sleep=clock.sleep)
+    srv.add_resident(np.zeros((200, 200)), "vortex", (200.0, 0.05, 100.0))
+    big = [S.Request(0, 0.0, 250, 20, "vortex"), S.Request(1, 0.0, 64, 20, "rotation")]
+    st = srv.run(big, max_wall=1e3)
+    res = {r.rid: r for r in srv.results}
+    assert st["requests"] == 2 and res[0].error == 2 and res[1].error == 0
+    assert clock.t < 1e3
+
+
 @pytest.mark.gpu
 def test_served_non_finite_request_fails_alone():
     from paper_2007_07760_gb300 import native as N

@@ -1,11 +1,11 @@
 """The allocation-free mass entry point against the context's own mass.
 
 dugks_field_mass_noalloc serves callers that cannot call cudaMalloc where they
-need a mass (during stream capture, under a framework that owns all device
-memory, in loops that cannot take cudaMalloc's implicit synchronisation). It
-keeps its per-tile partials in a static device array instead of allocated
-scratch. This file is collected last so that a failure here comes after every
-other test has run.
+need a mass (under a framework whose caching allocator owns all device memory,
+in loops that cannot take cudaMalloc's implicit synchronisation). It keeps its
+per-tile partials in a static device array instead of allocated scratch. This
+file is collected last so that a failure here comes after every other test has
+run.
 """
 import numpy as np
 import pytest
@@ -48,3 +48,19 @@ def test_noalloc_rejects_fields_beyond_its_scratch():
     code = N.dugks_field_mass_noalloc(field.data_ptr(), 0, 4097, 4096, 4097, out.data_ptr(), None)
     assert code == N.DUGKS_EINVAL
     assert N.dugks_field_mass_noalloc(field.data_ptr(), 2, 4, 4, 4, out.data_ptr(), None) == N.DUGKS_EINVAL
+
+
+def test_noalloc_serves_one_tile_column_at_the_tile_limit():
+    # 32 x 524288 cells: one tile column of 65536 tile rows (the array's limit),
+    # more tile rows than a grid's y dimension may hold
+    torch = pytest.importorskip("torch")
+    nx, ny = 32, 65536 * 8
+    g = torch.Generator(device="cuda").manual_seed(2007077609)
+    field = torch.rand((ny, nx), dtype=torch.float64, device="cuda", generator=g)
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        assert N.dugks_field_mass_noalloc(field.data_ptr(), 0, nx, ny, nx, out.data_ptr(), None) == N.DUGKS_OK
+        torch.cuda.synchronize()
+        ref = float(field.sum().item())
+        assert abs(float(out.item()) - ref) / ref < 1e-13
+        field.mul_(0.5)
