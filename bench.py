@@ -40,10 +40,16 @@ from paper_2007_07760_gb300 import workloads as WL  # noqa: E402
 
 METRIC = "D2Q9 cell-updates/s"
 UNIT = "cell-updates/s"
-BYTES_PER_CELL = {"fp64": 160, "fp32": 84, "fp16f": 48}   # two-stage, with d(phi u)/dt
-# three-stage: the two kernels of a step move 57 planes between them (FP64), 62 with
-# the FP32 phi planes
-BYTES_PER_CELL_T3 = {"fp64": 456, "fp32": 248}
+# Algorithmic bytes per cell-update (the roofline's numerator): the state read once
+# and written once per step. Two-stage with d(phi u)/dt: 9 distribution values read
+# and written plus phi of the older level read and phi of the new level written.
+BYTES_PER_CELL = {"fp64": 160, "fp32": 80, "fp16f": 48}
+# three-stage, two kernels per step: 56 values moved between them
+BYTES_PER_CELL_T3 = {"fp64": 448, "fp32": 224}
+# What this build's kernels actually move per cell (FP32 and FP16 storage keep phi
+# of the state as a plane of its own, read as well: +4 B; three-stage: the phi
+# planes of tilde f' and of the accumulator as well)
+BYTES_PER_CELL_ACTUAL = {("fp64", 2): 160, ("fp32", 2): 84, ("fp16f", 2): 48, ("fp64", 3): 456, ("fp32", 3): 248}
 
 
 def bytes_per_cell(precision: str, stages: int) -> int:
@@ -223,24 +229,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_single(solver, stream, warmup: int, K: int, dist=None, local: int = 0):
-    """W untimed and K timed steps of one solver, L2 flushed before each. One step
-    = the step kernel (per-tile FP64 mass partials) + the kernel that sums them;
-    the second is launched as a programmatic dependent of the first, so no event
-    sits between them in the timed pass. A second pass of K steps, with events
-    around the step kernel alone, gives its duration for the roofline."""
+def time_single(solver, stream, warmup: int, K: int, dist=None, local: int = 0, flush_l2: bool = True):
+    """W untimed and K timed steps of one solver, L2 flushed before each (unless
+    flush_l2 is false: a state larger than L2, or the L2-resident comparison). One
+    step = the step kernel (per-tile FP64 mass partials) + the kernel that sums
+    them; the second is launched as a programmatic dependent of the first, so no
+    event sits between them in the timed pass. A second pass of K steps, with
+    events around the step kernel alone, gives its duration for the roofline."""
     import torch
     from paper_2007_07760_gb300 import native as N
 
     mass_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4 if flush_l2 else 1, dtype=torch.float32, device="cuda")
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
     with torch.cuda.stream(stream):
         for _ in range(warmup):
-            flush.zero_()
+            if flush_l2:
+                flush.zero_()
             N.dugks_step(solver.ctx, 1)
             N.dugks_mass_device(solver.ctx, mass_dev.data_ptr())
     stream.synchronize()
@@ -252,13 +260,15 @@ def time_single(solver, stream, warmup: int, K: int, dist=None, local: int = 0):
     with ClockSampler(local) as clk:
         with torch.cuda.stream(stream):
             for a, b in whole:
-                flush.zero_()
+                if flush_l2:
+                    flush.zero_()
                 a.record(stream)
                 N.dugks_step(solver.ctx, 1)
                 N.dugks_mass_device(solver.ctx, mass_dev.data_ptr())
                 b.record(stream)
             for a, b in kern:
-                flush.zero_()
+                if flush_l2:
+                    flush.zero_()
                 a.record(stream)
                 N.dugks_step(solver.ctx, 1)
                 b.record(stream)
@@ -276,26 +286,43 @@ def time_single(solver, stream, warmup: int, K: int, dist=None, local: int = 0):
             "avg_step_ms": sum(a.elapsed_time(b) for a, b in kern) / K, "clocks": clocks, "mass": mass}
 
 
-def also_single(name: str, precision: str, K: int, generic: bool = False):
+def also_single(name: str, precision: str, K: int, generic: bool = False, flush_l2: bool = True,
+                tune: bool = False):
     """Secondary single-grid measurement for the "also" list of the JSON line."""
     import torch
     from paper_2007_07760_gb300 import native as N
 
     prob, desc = workload(name, precision)
     stream = torch.cuda.Stream()
+    variant = None
+    if tune and not generic:
+        from paper_2007_07760_gb300 import autotune
+        with N.Solver.from_problem(prob, precision=precision, stream=stream.cuda_stream) as solver:
+            variant = autotune.tune(solver, "single", prob.cells)
     with N.Solver.from_problem(prob, precision=precision, stream=stream.cuda_stream) as solver:
         if generic:
             solver.set_variant(-1)
-        r = time_single(solver, stream, 10, K)
+        elif variant is not None:
+            solver.set_variant(variant)
+        r = time_single(solver, stream, 10, K, flush_l2=flush_l2)
+        traffic = NCU_TRAFFIC.get((kernel_source_hash(), desc["workload"])) if not generic else None
     peak, _ = measured_peak_hbm()
     bpc = bytes_per_cell(precision, prob.stages)
     achieved = bpc * prob.cells / (r["avg_step_ms"] * 1e-3) / 1e9
-    return {"workload": desc["workload"] + ("_generic_kernel" if generic else ""), "bytes_per_cell": bpc,
-            "value": prob.cells * K / (r["total_ms"] * 1e-3), "unit": UNIT, "steps": K,
-            "ms_per_step": r["total_ms"] / K,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "avg_kernel_ms": r["avg_step_ms"]},
-            "clocks": r["clocks"]}
+    state_mb = BYTES_PER_CELL_ACTUAL[(precision, prob.stages)] * prob.cells / 1e6
+    out = {"workload": desc["workload"] + ("_generic_kernel" if generic else ""), "bytes_per_cell": bpc,
+           "bytes_per_cell_actual": BYTES_PER_CELL_ACTUAL[(precision, prob.stages)],
+           "value": prob.cells * K / (r["total_ms"] * 1e-3), "unit": UNIT, "steps": K,
+           "ms_per_step": r["total_ms"] / K,
+           "l2": ("flushed before every timed step" if flush_l2 else
+                  f"not flushed: steps back to back ({state_mb:.0f} MB of state"
+                  + (", far larger than the 129 MB L2)" if state_mb > 400 else ", L2-resident)")),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "traffic": traffic, "avg_kernel_ms": r["avg_step_ms"]},
+           "clocks": r["clocks"]}
+    if variant is not None:
+        out["tile_variant"] = variant
+    return out
 
 
 def run_ours(args):
@@ -381,7 +408,10 @@ def run_ours(args):
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp64": "f64", "fp32": "f32", "fp16f": "f32 (f16 storage)"}[args.precision],
             "data": "synthetic",
-            "config": dict(desc, l2="flushed before every timed step (512 MiB write, untimed)",
+            "config": dict(desc, l2="flushed before every timed step (512 MiB write, untimed); the step's 88 MB "
+                                    "of writes then stay in L2 during the launch and reach DRAM during the next "
+                                    "flush, so the DRAM traffic of a launch is its reads (see the 4096^2 line in "
+                                    "'also' for a state far larger than L2)",
                            mass="FP64 per-tile partials in the step kernel + fixed-order sum kernel",
                            replicas=world, parallelism="replicas" if world > 1 else "single"),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -389,8 +419,9 @@ def run_ours(args):
                          "kernel": desc.get("kernel", "step_fast_kernel (TMA-staged fused two-stage DUGKS step)"
                                             if prob.stages == 2 else
                                             "step_fast_kernel KIND_T3A + KIND_T3B (the two kernels of a three-stage step)"),
-                         "bytes_per_cell": bpc, "peak_source": peak_kind,
-                         "avg_kernel_ms": avg_step_ms},
+                         "bytes_per_cell": bpc,
+                         "bytes_per_cell_actual": BYTES_PER_CELL_ACTUAL[(args.precision, prob.stages)],
+                         "peak_source": peak_kind, "avg_kernel_ms": avg_step_ms},
             "e2e": e2e,
             "gpu_launches": launches_per_step * K,
             "clocks": clocks,
@@ -399,7 +430,10 @@ def run_ours(args):
         if cpu is not None:
             line["cpu_baseline"] = cpu
         if world == 1 and not args.no_also:
-            line["also"] = [also_single("slotted_disk256", "fp32", 300), also_batch(512, "fp32", 64),
+            line["also"] = [also_single("vortex4096", "fp32", 30, flush_l2=False, tune=True),
+                            also_batch(512, "fp32", 64),
+                            also_single(args.workload, args.precision, 100, flush_l2=False),
+                            also_single("slotted_disk256", "fp32", 300),
                             also_single(args.workload, "fp64", 20, generic=True),
                             also_single("vortex1024_t3", "fp32", 50), also_single("vortex1024_p4", "fp32", 50)]
         print(json.dumps(line), flush=True)
@@ -474,6 +508,7 @@ def run_batch(args, dist, world, rank, local):
     bpc = BYTES_PER_CELL[args.precision]
     achieved = bpc * cells / (total_ms / K * 1e-3) / 1e9
     tsize = 8 if args.precision == "fp64" else 4
+    traffic = NCU_TRAFFIC.get((kernel_source_hash(), desc["workload"]))
     e2e = {"value": job_rate(cells * K, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(cells * 8 / K), "d2h_bytes_per_step": int(cells * tsize / K),
            "path": "dugks_batch_add from host fields + K steps + dugks_batch_read_phi of every grid, amortised over K"}
@@ -484,8 +519,9 @@ def run_batch(args, dist, world, rank, local):
             "dtype": {"fp64": "f64", "fp32": "f32", "fp16f": "f32 (f16 storage)"}[args.precision],
             "data": "synthetic", "config": desc,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "batch_fast_kernel + batch_advance_kernel (graph-replayed)",
-                         "bytes_per_cell": bpc, "peak_source": peak_kind},
+                         "traffic": traffic, "kernel": "batch_fast_kernel + batch_advance_kernel (graph-replayed)",
+                         "bytes_per_cell": bpc, "bytes_per_cell_actual": BYTES_PER_CELL_ACTUAL[(args.precision, 2)],
+                         "peak_source": peak_kind},
             "e2e": e2e, "gpu_launches": 2 * K, "clocks": r["clocks"],
         }
         print(json.dumps(line), flush=True)
@@ -495,10 +531,14 @@ def also_batch(count: int, precision: str, K: int):
     r = measure_batch(count, precision, 8, K)
     peak, _ = measured_peak_hbm()
     achieved = BYTES_PER_CELL[precision] * r["cells"] / (r["total_ms"] / K * 1e-3) / 1e9
+    traffic = NCU_TRAFFIC.get((kernel_source_hash(), r["desc"]["workload"]))
     return {"workload": r["desc"]["workload"], "value": r["cells"] * K / (r["total_ms"] * 1e-3), "unit": UNIT,
             "steps": K, "ms_per_step": r["total_ms"] / K, "cells": r["cells"],
-            "tile_variant": r["desc"]["tile_variant"],
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak},
+            "tile_variant": r["desc"]["tile_variant"], "bytes_per_cell": BYTES_PER_CELL[precision],
+            "bytes_per_cell_actual": BYTES_PER_CELL_ACTUAL[(precision, 2)],
+            "l2": "no flush: the state of all grids is larger than L2",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic},
             "clocks": r["clocks"]}
 
 

@@ -113,11 +113,13 @@ def test_variants_fp32(oracle, order, flux, stages, cfl):
 
 
 def test_fp16_storage_error_bounded(oracle):
-    """FP16 deviation storage: error against the FP64 oracle, stated in DESIGN."""
+    """FP16 deviation storage (f - w phi in half precision, phi an FP32 plane):
+    error against the FP64 oracle after 1000 steps; measured 9.8e-6 on a GB300,
+    bound twice that."""
     prob = WL.drop64(order=3)
     phi, ref, m, mref = run_both(oracle, prob, 1000, precision="fp16f")
     err = np.abs(phi - ref).max()
-    assert err < 2e-3, err
+    assert err < 2e-5, err
     assert abs(m - mref) / mref < 1e-5
 
 
