@@ -46,7 +46,8 @@ typedef enum {
 
 enum { DUGKS_FP64 = 0, DUGKS_FP32 = 1, DUGKS_FP16F = 2 };
 enum { DUGKS_UPWIND = 0, DUGKS_CENTRAL = 1 };
-enum { DUGKS_VEL_UNIFORM = 0, DUGKS_VEL_ROTATION = 1, DUGKS_VEL_VORTEX = 2, DUGKS_VEL_FIELD = 3 };
+enum { DUGKS_VEL_UNIFORM = 0, DUGKS_VEL_ROTATION = 1, DUGKS_VEL_VORTEX = 2, DUGKS_VEL_FIELD = 3,
+       DUGKS_VEL_DEFORM = 4 };
 
 /* Problem statement (Sec. II-III): interface width W, mobility M, CFL number,
  * isotropic stencil order, face reconstruction, number of stages.
@@ -91,6 +92,9 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
  *                                v =  U sin^2(pi y/L) sin(2 pi x/L) cos(pi t/T)
  *   FIELD    u_host, v_host = ny * nx cell-centre components (copied); a face
  *            takes the mean of its two cells.
+ *   DEFORM   params = (L, U, T): the smoothed deformation of Sec. III.D,
+ *            u = -U sin(4 pi x/L) sin(4 pi y/L) cos(pi t/T),
+ *            v = -U cos(4 pi x/L) cos(4 pi y/L) cos(pi t/T).
  * Analytic fields are evaluated in the kernels at each point and time.
  * Allowed before the first step (it then defines the initial equilibrium) or
  * later (the new field applies from the next step). */

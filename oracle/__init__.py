@@ -84,7 +84,7 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-VEL_KINDS = {"uniform": 0, "rotation": 1, "vortex": 2, "field": 3, "reversing": 4}
+VEL_KINDS = {"uniform": 0, "rotation": 1, "vortex": 2, "field": 3, "reversing": 4, "deformation": 5}
 
 
 @dataclass

@@ -246,6 +246,13 @@ void orc_velocity(const orc_params *p, double x, double y, double t, double uv[2
         uv[1] = (1 - fx) * (1 - fy) * v00 + fx * (1 - fy) * v10 + (1 - fx) * fy * v01 + fx * fy * v11;
         return;
     }
+    case 5: { /* smoothed deformation (Sec. III.D): 4 x 4 cells of vortices on a box of side L,
+               * u = -U sin(4 pi x/L) sin(4 pi y/L) cos(pi t/T), v = -U cos(4 pi x/L) cos(4 pi y/L) cos(pi t/T) */
+        double L = p->vel[0], U = p->vel[1], T = p->vel[2], c = cos(PI * t / T);
+        uv[0] = -U * sin(4.0 * PI * x / L) * sin(4.0 * PI * y / L) * c;
+        uv[1] = -U * cos(4.0 * PI * x / L) * cos(4.0 * PI * y / L) * c;
+        return;
+    }
     case 4: { /* uniform flow reversed by the vortex's factor cos(pi t / T): test-only kind
                * whose exact displacement (ux, uy) T / pi sin(pi t / T) pins the time levels */
         double c = cos(PI * t / p->vel[2]);
@@ -444,7 +451,8 @@ int orc_check(const orc_params *p) {
     if (p->order < 2 || p->order > 4 || (p->flux != 0 && p->flux != 1)) return -1;
     if (p->stages != 2 && p->stages != 3) return -1;
     if (p->phiA == p->phiB) return -1;
-    if (p->vel_kind < 0 || p->vel_kind > 4) return -1;
+    if (p->vel_kind < 0 || p->vel_kind > 5) return -1;
+    if (p->vel_kind == 5 && (p->vel[0] <= 0 || p->vel[2] <= 0)) return -1;
     if (p->vel_kind == 3 && (!p->u_field || !p->v_field)) return -1;
     if (p->vel_kind == 2 && (p->vel[0] <= 0 || p->vel[2] <= 0)) return -1;
     if (p->vel_kind == 4 && !(p->vel[2] > 0)) return -1;

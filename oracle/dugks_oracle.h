@@ -32,9 +32,11 @@ typedef struct {
     int dtphiu;      /* 1 = keep the d(phi u)/dt part of the source Eq. (14b) */
     double phiA, phiB;
     int vel_kind;    /* 0 uniform, 1 rigid rotation, 2 single vortex, 3 cell field,
-                        4 reversing uniform (test-only: pins the time levels) */
+                        4 reversing uniform (test-only: pins the time levels),
+                        5 smoothed deformation (Sec. III.D) */
     double vel[4];   /* uniform (ux, uy); rotation (cx, cy, omega); vortex (L, U, T);
-                        reversing uniform (ux, uy, T): (ux, uy) cos(pi t / T) */
+                        reversing uniform (ux, uy, T): (ux, uy) cos(pi t / T);
+                        deformation (L, U, T) */
     const double *u_field, *v_field;   /* vel_kind 3: cell-centre components */
 } orc_params;
 

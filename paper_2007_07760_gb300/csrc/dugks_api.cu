@@ -176,12 +176,13 @@ int ensure_init(dugks_ctx *c) {
     }
 }
 
-// Single-vortex reversal factors cos(pi t / T) at the cell time, the older time
-// of d(phi u)/dt and the face time (FP64 on the host); zero for other velocities.
+// Reversal factors cos(pi t / T) of the single vortex and of the deformation at
+// the cell time, the older time of d(phi u)/dt and the face time (FP64 on the
+// host); zero for other velocities.
 template <typename T>
 FastExtra<T> vortex_factors(const dugks_ctx *c, double t, double t_old, double t_face) {
     FastExtra<T> fx{};
-    if (c->vel_kind == DUGKS_VEL_VORTEX) {
+    if (c->vel_kind == DUGKS_VEL_VORTEX || c->vel_kind == DUGKS_VEL_DEFORM) {
         const double PI = 3.14159265358979323846, Tp = c->vel[2];
         fx.vc_t = (T)std::cos(PI * t / Tp);
         fx.vc_told = (T)std::cos(PI * t_old / Tp);
@@ -251,13 +252,7 @@ int step_t2(dugks_ctx *c, double *dbg = nullptr) {
             c->coef_h = h;
         }
         const FaceCoefs<T> &cf = *reinterpret_cast<const FaceCoefs<T> *>(c->coefs.data());
-        FastExtra<T> fx{};
-        if (c->vel_kind == DUGKS_VEL_VORTEX) {   // reversal factor cos(pi t / T), in FP64
-            const double PI = 3.14159265358979323846, Tp = c->vel[2];
-            fx.vc_t = (T)std::cos(PI * t / Tp);
-            fx.vc_told = (T)std::cos(PI * (t - dt) / Tp);
-            fx.vc_tface = (T)std::cos(PI * (t + h) / Tp);
-        }
+        const FastExtra<T> fx = vortex_factors<T>(c, t, t - dt, t + h);
         e = Launch<T, ST>::step_fast(q, cf, fx, c->tmX[c->cur], c->tmPhi[iPo], c->tmPhi[iPc], c->p.order,
                                      c->p.flux, c->variant, c->stream);
     } else {
@@ -638,6 +633,11 @@ int dugks_set_velocity(dugks_ctx *c, int kind, const double *params, const doubl
         break;
     case DUGKS_VEL_VORTEX:
         if (!params || !(params[0] > 0) || !(params[2] > 0)) return fail(c, DUGKS_EINVAL, "vortex needs (L > 0, U, T > 0)");
+        v[0] = params[0]; v[1] = params[1]; v[2] = params[2];
+        break;
+    case DUGKS_VEL_DEFORM:
+        if (!params || !(params[0] > 0) || !(params[2] > 0))
+            return fail(c, DUGKS_EINVAL, "deformation needs (L > 0, U, T > 0)");
         v[0] = params[0]; v[1] = params[1]; v[2] = params[2];
         break;
     case DUGKS_VEL_FIELD: {

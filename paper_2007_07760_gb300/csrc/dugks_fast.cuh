@@ -139,7 +139,7 @@ __host__ __device__ constexpr bool tap_zero(int order, int flux, TapIdx w) {
 // Per-step scalars of the fast kernel that the generic parameters do not carry.
 template <typename T>
 struct FastExtra {
-    T vc_t, vc_told, vc_tface;   // vortex reversal factors cos(pi t / T) at t, t_old, t_face
+    T vc_t, vc_told, vc_tface;   // reversal factors cos(pi t / T) at t, t_old, t_face (vortex, deformation)
 };
 
 // ---- TMA and mbarrier (inline PTX) -------------------------------------------
@@ -411,6 +411,11 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             const T Ay = where == 2 ? sAyf[j] : sAyc[j], By = where == 2 ? sByf[j] : sByc[j];
             u = -p.vp1 * Ax * By * vc;
             v = p.vp1 * Ay * Bx * vc;
+        } else if (p.vel_kind == VEL_DEFORM) {   // spatial part times the reversal factor vc
+            const int gx = wrap_small(x0 + x, nx), gy = wrap_small(y0 + y, ny);
+            deform_spatial(p, T(gx) + (where == 1 ? T(1) : T(0.5)), T(gy) + (where == 2 ? T(1) : T(0.5)), u, v);
+            u *= vc;
+            v *= vc;
         } else {
             const int gx = wrap_small(x0 + x, nx), gy = wrap_small(y0 + y, ny);
             if (where == 0) vel_cell(p, gx, gy, t, u, v);
@@ -438,9 +443,10 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             nyv = gyp * inv;
         }
         const T theta = p.theta_c * (ph - p.phiA) * (ph - p.phiB);  // Eq. (4)
-        // the velocity at the cell centre at both time levels: the vortex's spatial
-        // part once, scaled by its reversal factor; the other kinds do not depend on t
-        const bool vortex = p.vel_kind == VEL_VORTEX;
+        // the velocity at the cell centre at both time levels: the spatial part of the
+        // vortex and of the deformation once, scaled by their reversal factors; the
+        // other kinds do not depend on t
+        const bool vortex = p.vel_kind == VEL_VORTEX || p.vel_kind == VEL_DEFORM;
         T u0, v0;
         vel(x, y, 0, p.t, vortex ? T(1) : fe_.vc_t, u0, v0);
         const T u = vortex ? u0 * fe_.vc_t : u0, v = vortex ? v0 * fe_.vc_t : v0;

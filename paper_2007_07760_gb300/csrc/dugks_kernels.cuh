@@ -41,7 +41,7 @@ __host__ __device__ __forceinline__ constexpr T wq(int k) {
 }
 
 enum Kind { KIND_T2 = 0, KIND_T3A = 1, KIND_T3B = 2 };
-enum Vel { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_FIELD = 3 };
+enum Vel { VEL_UNIFORM = 0, VEL_ROTATION = 1, VEL_VORTEX = 2, VEL_FIELD = 3, VEL_DEFORM = 4 };
 
 // Storage of the distribution and of phi:
 //  * Store<double, double>: full FP64 values; phi of a state is sum_k X_k
@@ -159,6 +159,18 @@ __device__ __forceinline__ double cospi_(double x) { return cospi(x); }
 template <>
 __device__ __forceinline__ float cospi_(float x) { return cospif(x); }
 
+// smoothed deformation of Sec. III.D without its reversal factor: 4 x 4 cells of
+// vortices on a box of side L, u = -U sin(4 pi x/L) sin(4 pi y/L),
+// v = -U cos(4 pi x/L) cos(4 pi y/L)
+template <typename T>
+__device__ __forceinline__ void deform_spatial(const StepParams<T> &p, T x, T y, T &u, T &v) {
+    const T L = p.vp0, U = p.vp1;
+    const T sx = sinpi_(T(4) * x / L), sy = sinpi_(T(4) * y / L);
+    const T cx = cospi_(T(4) * x / L), cy = cospi_(T(4) * y / L);
+    u = -U * sx * sy;
+    v = -U * cx * cy;
+}
+
 template <typename T>
 __device__ __forceinline__ void vel_analytic(const StepParams<T> &p, T x, T y, T t, T &u, T &v) {
     if (p.vel_kind == VEL_UNIFORM) {
@@ -167,6 +179,11 @@ __device__ __forceinline__ void vel_analytic(const StepParams<T> &p, T x, T y, T
     } else if (p.vel_kind == VEL_ROTATION) {
         u = -p.vp2 * (y - p.vp1);
         v = p.vp2 * (x - p.vp0);
+    } else if (p.vel_kind == VEL_DEFORM) {   // reversed by cos(pi t / T)
+        deform_spatial(p, x, y, u, v);
+        const T c = cospi_(t / p.vp2);
+        u *= c;
+        v *= c;
     } else {  // single vortex, period box L, amplitude U, reversal period T
         const T L = p.vp0, U = p.vp1;
         const T sx = sinpi_(x / L), sy = sinpi_(y / L), c = cospi_(t / p.vp2);

@@ -17,9 +17,9 @@ DUGKS_OK, DUGKS_EINVAL, DUGKS_ENOMEM, DUGKS_ECUDA, DUGKS_ETIMEOUT, DUGKS_ENONFIN
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "ESTATE"}
 DUGKS_FP64, DUGKS_FP32, DUGKS_FP16F = 0, 1, 2
 DUGKS_UPWIND, DUGKS_CENTRAL = 0, 1
-DUGKS_VEL_UNIFORM, DUGKS_VEL_ROTATION, DUGKS_VEL_VORTEX, DUGKS_VEL_FIELD = 0, 1, 2, 3
+DUGKS_VEL_UNIFORM, DUGKS_VEL_ROTATION, DUGKS_VEL_VORTEX, DUGKS_VEL_FIELD, DUGKS_VEL_DEFORM = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": DUGKS_FP64, "fp32": DUGKS_FP32, "fp16f": DUGKS_FP16F}
-VEL_KINDS = {"uniform": 0, "rotation": 1, "vortex": 2, "field": 3}
+VEL_KINDS = {"uniform": 0, "rotation": 1, "vortex": 2, "field": 3, "deformation": 4}
 
 
 class dugks_params(ctypes.Structure):

@@ -156,6 +156,47 @@ def extension(Pe: float, cfl: float, L0: int = 256, M: float = 0.02, W: float = 
     return phi0, u, v, int(round(L0 / U0 / cfl))
 
 
+def zalesak_disk(L0: int = 256) -> np.ndarray:
+    """Zalesak's slotted disk of Sec. III.B as a step function: phi = 1 at the cell
+    centres inside the disk (radius 0.4 L0, centred in the L0 x L0 domain) and
+    outside the slot (0.08 L0 wide, opening downward), 0 elsewhere. Reading: the
+    slot length is unstated; it runs from the bottom of the disk to 0.25 R above
+    the centre (length 1.25 R), the proportions of the slotted-disk workload."""
+    R, w = 0.4 * L0, 0.08 * L0
+    X, Y = centres(L0, L0)
+    c = 0.5 * L0
+    inside = (X - c) ** 2 + (Y - c) ** 2 < R * R
+    slot = (np.abs(X - c) < 0.5 * w) & (Y < c + 0.25 * R)
+    return (inside & ~slot).astype(np.float64)
+
+
+def zalesak(Pe: float, cfl: float, M: float = 0.02, L0: int = 256, Cn: float = 4.0 / 256):
+    """Zalesak's disk rotation (Sec. III.B): rigid rotation about the domain centre
+    with u = -(U0 pi / L0)(y - L0/2), v = (U0 pi / L0)(x - L0/2), U0 = Pe M / L0,
+    one revolution in T = 2 T_f = 2 L0 / U0; W = Cn L0. Returns the problem (its
+    steps = one revolution)."""
+    U0 = Pe * M / L0
+    om = U0 * math.pi / L0
+    steps = int(round(2.0 * L0 / U0 / cfl))
+    return Problem(f"zalesak{L0}", L0, L0, Cn * L0, M, cfl, 3, 0, 2, "rotation", (0.5 * L0, 0.5 * L0, om),
+                   zalesak_disk(L0), steps)
+
+
+def deformation(Pe: float, cfl: float, M: float = 0.02, L0: int = 512, Cn: float = 4.0 / 512):
+    """Smoothed deformation (Sec. III.D): a circle in the centre of the L0 x L0
+    domain in the shear flow u = -U0 sin(4 pi x/L0) sin(4 pi y/L0) cos(pi t/T_f),
+    v = -U0 cos(4 pi x/L0) cos(4 pi y/L0) cos(pi t/T_f), U0 = Pe M / L0, run to
+    t = T_f = L0 / U0 (the displacement integral of cos(pi t / T_f) vanishes there).
+    Reading: the circle's radius is unstated; R = L0/5 as in the paper's other
+    tests. Returns the problem (its steps reach T_f)."""
+    U0 = Pe * M / L0
+    Tf = L0 / U0
+    steps = int(round(Tf / cfl))
+    phi0 = drops(L0, L0, [(0.5 * L0, 0.5 * L0)], [L0 / 5], Cn * L0)
+    return Problem(f"deformation{L0}", L0, L0, Cn * L0, M, cfl, 3, 0, 2, "deformation", (float(L0), U0, steps * cfl),
+                   phi0, steps)
+
+
 def translation(n: int, order: int, flux: int, stages: int, cfl: float,
                 Pe: float = 128.0, Cn: float = 1.0 / 32, M: float = 0.02) -> Problem:
     """Diagonal translation of a circle R = L0/5 (Sec. III.A): U0 = Pe M / L0,

@@ -72,12 +72,33 @@ def test_variants_fp64_ragged(oracle, order, flux, stages, cfl):
     assert abs(m - mref) / mref < 1e-13
 
 
-@pytest.mark.parametrize("kind,vel", [("rotation", (20.0, 14.0, 2e-3)), ("vortex", (40.0, 0.05, 30.0))])
+@pytest.mark.parametrize("kind,vel", [("rotation", (20.0, 14.0, 2e-3)), ("vortex", (40.0, 0.05, 30.0)),
+                                      ("deformation", (40.0, 0.05, 30.0))])
 @pytest.mark.parametrize("stages", [2, 3])
 def test_velocity_kinds_fp64(oracle, kind, vel, stages):
     prob = small(40, 28, 3, 0, stages, 0.8 if stages == 2 else 0.5, vel_kind=kind, vel=vel, seed=7)
     phi, ref, _, _ = run_both(oracle, prob, 60)
     assert rel_err(phi, ref) < FP64_TOL
+
+
+@pytest.mark.parametrize("precision,variant", [("fp64", 2), ("fp64", -1), ("fp32", 4), ("fp32", -1)])
+@pytest.mark.parametrize("order,flux", [(3, 0), (2, 1), (4, 0)])
+def test_deformation_flow_every_kernel(oracle, precision, variant, order, flux):
+    """The smoothed deformation of Sec. III.D (time-dependent: reversed by cos(pi t/T))
+    through the TMA-staged and the generic kernels, with the reversal inside the run."""
+    prob = small(64, 48, order, flux, 2, 0.8, vel_kind="deformation", vel=(64.0, 0.05, 24.0), seed=13)
+    ref = O_run(oracle, prob, 50)
+    with N.Solver.from_problem(prob, precision=precision) as s:
+        s.set_variant(variant)
+        s.step(50)
+        assert s.status() == 0
+        phi = s.phi()
+    err = np.abs(phi - ref).max()
+    assert (err / np.abs(ref).max() if precision == "fp64" else err) < (FP64_TOL if precision == "fp64" else FP32_TOL)
+
+
+def O_run(O, prob, steps):
+    return O.State(oracle_params(O, prob), prob.phi0).run(steps).phi()
 
 
 def test_velocity_field_fp64(oracle):

@@ -3,7 +3,8 @@ the step evaluates them (Sec. II.A: u prescribed and divergence free; Eq. (14b):
 the d(phi u)/dt source; Eqs. (24)-(28): faces at t_n + h; Sec. II.B.2: the
 three-stage faces at t_n + dt/6 and t_n + 3 dt/4 and the cell stage at t').
 
-* Every analytic field is checked against a stream function psi, written here
+* Every analytic field (rotation, single vortex, the smoothed deformation of
+  Sec. III.D) is checked against a stream function psi, written here
   independently of the oracle's formulas: u = -d psi / dy, v = d psi / dx, taken
   by central differences of psi. That fixes sign, axis, amplitude and the
   cos(pi t / T) reversal, and makes the fields divergence free by construction;
@@ -37,6 +38,13 @@ def _psi_rotation(cx, cy, om):
     return lambda x, y, t: 0.5 * om * ((x - cx) ** 2 + (y - cy) ** 2)
 
 
+def _psi_deformation(L, U, T):
+    # u = -U sin(4 pi x/L) sin(4 pi y/L) c(t), v = -U cos(4 pi x/L) cos(4 pi y/L) c(t)
+    # derive from psi = -(U L / 4 pi) sin(4 pi x/L) cos(4 pi y/L) cos(pi t/T)
+    a = 4 * np.pi / L
+    return lambda x, y, t: -U / a * np.sin(a * x) * np.cos(a * y) * np.cos(np.pi * t / T)
+
+
 def _from_psi(psi, x, y, t, e=1e-4):
     return np.array([-(psi(x, y + e, t) - psi(x, y - e, t)) / (2 * e),
                      (psi(x + e, y, t) - psi(x - e, y, t)) / (2 * e)])
@@ -47,12 +55,14 @@ def _from_psi(psi, x, y, t, e=1e-4):
     ("vortex", (1.0, 1.3, 8.0), _psi_vortex(1.0, 1.3, 8.0)),
     ("rotation", (128.0, 128.0, 2 * np.pi / 13107.2), _psi_rotation(128.0, 128.0, 2 * np.pi / 13107.2)),
     ("rotation", (3.0, -2.0, -0.7), _psi_rotation(3.0, -2.0, -0.7)),
+    ("deformation", (512.0, 0.04, 12800.0), _psi_deformation(512.0, 0.04, 12800.0)),
+    ("deformation", (64.0, 1.0, 3.0), _psi_deformation(64.0, 1.0, 3.0)),
 ])
 def test_velocity_is_the_curl_of_its_stream_function(oracle, kind, vel, psi):
     p = oracle.Params(16, 16, vel_kind=kind, vel=vel)
     rng = np.random.default_rng(2007077611)
-    scale = vel[0] if kind == "vortex" else 100.0
-    T = vel[2] if kind == "vortex" else 1.0
+    scale = vel[0] if kind in ("vortex", "deformation") else 100.0
+    T = vel[2] if kind in ("vortex", "deformation") else 1.0
     for _ in range(200):
         x, y = rng.uniform(-0.5, 1.5, 2) * scale
         t = rng.uniform(0, 2.5) * T
@@ -75,7 +85,8 @@ def test_vortex_reverses_and_vanishes_at_half_period(oracle):
         np.testing.assert_allclose(oracle.velocity(p, x, y, 2 * T), u0, atol=1e-16)
 
 
-@pytest.mark.parametrize("kind,vel", [("vortex", (64.0, 0.05, 50.0)), ("rotation", (20.0, 30.0, 0.01))])
+@pytest.mark.parametrize("kind,vel", [("vortex", (64.0, 0.05, 50.0)), ("rotation", (20.0, 30.0, 0.01)),
+                                      ("deformation", (256.0, 0.05, 50.0))])
 def test_discrete_divergence_vanishes(oracle, kind, vel):
     p = oracle.Params(16, 16, vel_kind=kind, vel=vel)
     rng = np.random.default_rng(11)
@@ -85,8 +96,9 @@ def test_discrete_divergence_vanishes(oracle, kind, vel):
             du = oracle.velocity(p, x + e, y, 3.0)[0] - oracle.velocity(p, x - e, y, 3.0)[0]
             dv = oracle.velocity(p, x, y + e, 3.0)[1] - oracle.velocity(p, x, y - e, 3.0)[1]
             worst = max(worst, abs(du + dv) / (2 * e))
-        # exactly zero for the rotation; second-order truncation (~ U (pi/L)^3 e^2) for the vortex
-        assert worst < (1e-15 if kind == "rotation" else 4 * 0.05 * (np.pi / 64) ** 3 * e * e + 1e-16)
+        # exactly zero for the rotation; second-order truncation (~ U k^3 e^2) for the others
+        k = np.pi / 64 if kind == "vortex" else 4 * np.pi / 256
+        assert worst < (1e-15 if kind == "rotation" else 4 * 0.05 * k ** 3 * e * e + 1e-16)
 
 
 def test_cell_field_face_value_is_the_mean_of_its_cells(oracle):
