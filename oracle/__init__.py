@@ -60,6 +60,7 @@ def lib():
         L = ctypes.CDLL(_LIB)
         P = ctypes.POINTER(_Params)
         D = ctypes.POINTER(ctypes.c_double)
+        L.orc_run_lbm.argtypes = [P, D, D, ctypes.c_long, ctypes.c_long]
         L.orc_stencil.argtypes = [ctypes.c_int, ctypes.c_int, D]
         L.orc_derivative.argtypes = [ctypes.c_int, ctypes.c_int, D, ctypes.c_int, ctypes.c_int, D]
         L.orc_velocity.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, D]
@@ -232,6 +233,14 @@ class State:
     def run(self, nsteps: int) -> "State":
         if lib().orc_run(ctypes.byref(self._pc), _ptr(self.f), _ptr(self.phi_prev),
                          self.step_index, int(nsteps)):
+            raise ValueError("invalid parameters")
+        self.step_index += int(nsteps)
+        return self
+
+    def run_lbm(self, nsteps: int) -> "State":
+        """The lattice Boltzmann method (stages = 1, cfl = 1): plain streaming."""
+        if lib().orc_run_lbm(ctypes.byref(self._pc), _ptr(self.f), _ptr(self.phi_prev),
+                             self.step_index, int(nsteps)):
             raise ValueError("invalid parameters")
         self.step_index += int(nsteps)
         return self

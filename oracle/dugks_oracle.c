@@ -449,7 +449,7 @@ int orc_check(const orc_params *p) {
     if (p->nx < 8 || p->ny < 8) return -1;
     if (!(p->W > 0) || !(p->M > 0) || !(p->cfl > 0) || p->cfl > 1.0) return -1;
     if (p->order < 2 || p->order > 4 || (p->flux != 0 && p->flux != 1)) return -1;
-    if (p->stages != 2 && p->stages != 3) return -1;
+    if (p->stages < 1 || p->stages > 3) return -1;   /* 1: streaming-collision DVM (Sec. II.B.1) */
     if (p->phiA == p->phiB) return -1;
     if (p->vel_kind < 0 || p->vel_kind > 5) return -1;
     if (p->vel_kind == 5 && (p->vel[0] <= 0 || p->vel[2] <= 0)) return -1;
@@ -560,6 +560,83 @@ static int step_once(const orc_params *p, double *X, double *phi_prev, long n) {
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Streaming-collision DVM (Sec. II.B.1, Eqs. (8)-(14)). State: tilde f^+ of   */
+/* Eq. (9) at the cell centres; phi_prev = phi at t.                          */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. (11b) and Eqs. (13)-(14): phi(t + dt) from the streamed tilde f', the cell
+ * quantities at t + dt (d(phi u)/dt by the backward difference from t, as for
+ * DUGKS), and the collision
+ * tilde f^+ = tilde f' + 2 dt/(2 tau + dt) (f^eq + tau S - tilde f'). */
+static void dvm_collide(const orc_params *p, double *X, const double *Fs, double *phi_prev, double t, double dt) {
+    const size_t N = (size_t)p->nx * p->ny;
+    const double tau = p->M / RT;
+    double *phi = malloc(N * sizeof(double)), *V = malloc(2 * N * sizeof(double));
+    double *g = malloc(9 * N * sizeof(double));
+    orc_phi(p, Fs, phi);   /* Eq. (13). Reading: the unweighted sum, as for Eq. (28) */
+    orc_cell_quantities(p, phi, phi_prev, t + dt, t, dt, p->dtphiu, V, g);
+    const double beta = 2.0 * dt / (2.0 * tau + dt);
+    for (size_t q = 0; q < 9 * N; q++) X[q] = Fs[q] + beta * (g[q] - Fs[q]);
+    memcpy(phi_prev, phi, N * sizeof(double));
+    free(phi); free(V); free(g);
+}
+
+/* One DVM step: Eq. (11a) streaming, tilde f'_k(x_c) = tilde f^+_k(x_c - xi_k dt),
+ * the value at the back-traced point taken from the Taylor expansion of Eq. (12)
+ * about the centre x_n of the cell that contains it. Reading: Eq. (12) prints
+ * "(.)^2 : grad^2" without the 1/2 of a Taylor series (as Eq. (26)); the cell
+ * holding x_c - xi_k dt is the neighbour x_c - xi_k for dt >= 1/2 (the paper's
+ * "starting cell just adjacent to the targeting cell"; at dt = 1/2 the point is on
+ * the cell edge and the neighbour is taken) and x_c itself below. Then Eq. (11b). */
+static void dvm_step(const orc_params *p, double *X, double *phi_prev, long n) {
+    const int nx = p->nx, ny = p->ny;
+    const size_t N = (size_t)nx * ny;
+    const double dt = p->cfl, t = n * dt;
+    const int s = dt >= 0.5 ? 1 : 0;
+    double *Fs = malloc(9 * N * sizeof(double)), *buf = malloc(9 * N * sizeof(double));
+    deriv_set D;
+    D.gx = buf; D.gy = buf + N; D.hxx = buf + 2 * N; D.hxy = buf + 3 * N; D.hyy = buf + 4 * N;
+    D.txxx = buf + 5 * N; D.txxy = buf + 6 * N; D.txyy = buf + 7 * N; D.tyyy = buf + 8 * N;
+    double *planes[9] = {D.gx, D.gy, D.hxx, D.hxy, D.hyy, D.txxx, D.txxy, D.txyy, D.tyyy};
+    const int nd = p->order == 2 ? 2 : (p->order == 3 ? 5 : 9);
+    for (int k = 0; k < Q; k++) {
+        D.F = X + k * N;
+        for (int w = 0; w < nd; w++) orc_derivative(p->order, w, D.F, nx, ny, planes[w]);
+        /* displacement from x_n = x_c - s xi_k to x_c - xi_k dt */
+        const double dx = EX[k] * (s - dt), dy = EY[k] * (s - dt);
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++)
+                Fs[k * N + (size_t)j * nx + i] = taylor(p, &D, idx(p, i - s * EX[k], j - s * EY[k]), dx, dy);
+    }
+    dvm_collide(p, X, Fs, phi_prev, t, dt);
+    free(Fs);
+    free(buf);
+}
+
+/* The lattice Boltzmann step (dt = 1): plain streaming from the neighbour
+ * x_c - xi_k, then the same collision. Written independently of the Taylor
+ * streaming above so that "the DVM at C = 1 is the LBM" (Sec. III.A) is a check
+ * between two codes. */
+static void lbm_step(const orc_params *p, double *X, double *phi_prev, long n) {
+    const int nx = p->nx, ny = p->ny;
+    const size_t N = (size_t)nx * ny;
+    double *Fs = malloc(9 * N * sizeof(double));
+    for (int k = 0; k < Q; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++)
+                Fs[k * N + (size_t)j * nx + i] = X[k * N + idx(p, i - EX[k], j - EY[k])];
+    dvm_collide(p, X, Fs, phi_prev, (double)n, 1.0);
+    free(Fs);
+}
+
+int orc_run_lbm(const orc_params *p, double *state, double *phi_prev, long step0, long nsteps) {
+    if (orc_check(p) || p->stages != 1 || p->cfl != 1.0) return -1;
+    for (long s = 0; s < nsteps; s++) lbm_step(p, state, phi_prev, step0 + s);
+    return 0;
+}
+
 int orc_init(const orc_params *p, const double *phi0, double *state, double *phi_prev) {
     if (orc_check(p)) return -1;
     const int nx = p->nx, ny = p->ny;
@@ -568,7 +645,8 @@ int orc_init(const orc_params *p, const double *phi0, double *state, double *phi
     double *V = malloc(2 * N * sizeof(double)), *g = malloc(9 * N * sizeof(double));
     /* Reading: start from f = f^eq (Omega = 0) with D = 0. */
     orc_cell_quantities(p, phi0, phi0, 0.0, 0.0, dt, 0, V, g);
-    const double frac = p->stages == 2 ? 0.5 : 0.25;   /* tilde f or hat f, Eq. (19) */
+    /* tilde f or hat f, Eq. (19); the DVM's tilde f^+ = f + (dt/2)(Omega + S), Eq. (9) */
+    const double frac = p->stages == 2 ? 0.5 : p->stages == 3 ? 0.25 : -0.5;
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             size_t c = (size_t)j * nx + i;
@@ -588,7 +666,10 @@ int orc_init(const orc_params *p, const double *phi0, double *state, double *phi
 
 int orc_run(const orc_params *p, double *state, double *phi_prev, long step0, long nsteps) {
     if (orc_check(p)) return -1;
-    for (long s = 0; s < nsteps; s++) step_once(p, state, phi_prev, step0 + s);
+    for (long s = 0; s < nsteps; s++) {
+        if (p->stages == 1) dvm_step(p, state, phi_prev, step0 + s);
+        else step_once(p, state, phi_prev, step0 + s);
+    }
     return 0;
 }
 

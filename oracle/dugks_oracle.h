@@ -28,7 +28,8 @@ typedef struct {
     double cfl;      /* CFL number C; dt = C dx / sqrt(3 RT) = C, Eq. (39) */
     int order;       /* 2, 3 or 4 */
     int flux;        /* 0 = upwind Eq. (26), 1 = central Eq. (25) */
-    int stages;      /* 2 = original DUGKS, 3 = three-stage third-order DUGKS */
+    int stages;      /* 2 = original DUGKS, 3 = three-stage third-order DUGKS,
+                        1 = streaming-collision DVM (Sec. II.B.1; flux unused) */
     int dtphiu;      /* 1 = keep the d(phi u)/dt part of the source Eq. (14b) */
     double phiA, phiB;
     int vel_kind;    /* 0 uniform, 1 rigid rotation, 2 single vortex, 3 cell field,
@@ -73,12 +74,17 @@ void orc_flux(const orc_params *p, const double *fE, const double *fN, double *L
 /* phi = sum_k X_k. */
 void orc_phi(const orc_params *p, const double *X, double *phi);
 
-/* Initial state from phi0: f = f^eq, state = f^eq - (dt/2) S (two-stage) or
- * f^eq - (dt/4) S (three-stage); phi_prev = phi0. Returns 0 or -1 (bad params). */
+/* Initial state from phi0: f = f^eq, state = f^eq - (dt/2) S (two-stage),
+ * f^eq - (dt/4) S (three-stage) or f^eq + (dt/2) S (DVM); phi_prev = phi0.
+ * Returns 0 or -1 (bad params). */
 int orc_init(const orc_params *p, const double *phi0, double *state, double *phi_prev);
 
 /* Advance nsteps full time steps starting at step index step0. Returns 0 or -1. */
 int orc_run(const orc_params *p, double *state, double *phi_prev, long step0, long nsteps);
+
+/* The lattice Boltzmann method (stages = 1, cfl = 1): plain streaming from the
+ * neighbour cell, then the DVM's collision. Returns 0 or -1. */
+int orc_run_lbm(const orc_params *p, double *state, double *phi_prev, long step0, long nsteps);
 
 /* Sum of phi over all cells. */
 double orc_mass(const orc_params *p, const double *state);
