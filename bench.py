@@ -49,11 +49,14 @@ BYTES_PER_CELL_T3 = {"fp64": 448, "fp32": 224}
 # What this build's kernels actually move per cell (FP32 and FP16 storage keep phi
 # of the state as a plane of its own, read as well: +4 B; three-stage: the phi
 # planes of tilde f' and of the accumulator as well)
-BYTES_PER_CELL_ACTUAL = {("fp64", 2): 160, ("fp32", 2): 84, ("fp16f", 2): 48, ("fp64", 3): 456, ("fp32", 3): 248}
+BYTES_PER_CELL_ACTUAL = {("fp64", 2): 160, ("fp32", 2): 84, ("fp16f", 2): 48, ("fp64", 3): 456, ("fp32", 3): 248,
+                         ("fp64", 1): 160, ("fp32", 1): 80}
+# the streaming-collision DVM (stages = 1) moves the same state as the two-stage step:
+# 9 values read and written, phi of the older level read, the new phi written
 
 
 def bytes_per_cell(precision: str, stages: int) -> int:
-    return BYTES_PER_CELL[precision] if stages == 2 else BYTES_PER_CELL_T3[precision]
+    return BYTES_PER_CELL[precision] if stages <= 2 else BYTES_PER_CELL_T3[precision]
 L2_FLUSH_BYTES = 512 << 20
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes) of one step
@@ -79,20 +82,23 @@ def workload(name: str, precision: str):
     if name == "slotted_disk256":
         prob = WL.slotted_disk256(order=3, flux=0, stages=2)
     elif name.startswith("vortex"):
-        # vortex<n>[_p<order>][_central][_t3]: the three-stage scheme at cfl 0.5 (it needs dt < 12 tau)
+        # vortex<n>[_p<order>][_central][_t3 | _dvm | _lbm]: the three-stage scheme at cfl 0.5 (it needs
+        # dt < 12 tau); the streaming-collision DVM at cfl 0.8, the LBM (the DVM at cfl 1)
         parts = name.split("_")
         n = int(parts[0][len("vortex"):] or 1024)
         order = next((int(q[1:]) for q in parts[1:] if q.startswith("p")), 3)
         flux = 1 if "central" in parts[1:] else 0
-        stages = 3 if "t3" in parts[1:] else 2
-        prob = WL.vortex1024(order=order, flux=flux, stages=stages, cfl=0.5 if stages == 3 else 0.8, n=n)
-        prob.name = parts[0]
+        stages = 3 if "t3" in parts[1:] else 1 if ("dvm" in parts[1:] or "lbm" in parts[1:]) else 2
+        cfl = 0.5 if stages == 3 else 1.0 if "lbm" in parts[1:] else 0.8
+        prob = WL.vortex1024(order=order, flux=flux, stages=stages, cfl=cfl, n=n)
+        prob.name = parts[0] + ("_lbm" if "lbm" in parts[1:] else "_dvm" if "dvm" in parts[1:] else "")
     elif name == "drop64":
         prob = WL.drop64()
     else:
         raise SystemExit(f"unknown workload {name}")
-    desc = {"workload": f"{prob.name}_{precision}_p{prob.order}_{'upwind' if prob.flux == 0 else 'central'}"
-                        f"_{prob.stages}stage",
+    scheme = (f"{'upwind' if prob.flux == 0 else 'central'}_{prob.stages}stage" if prob.stages > 1 else
+              "streaming_collision")
+    desc = {"workload": f"{prob.name}_{precision}_p{prob.order}_{scheme}",
             "nx": prob.nx, "ny": prob.ny, "order": prob.order,
             "flux": "upwind" if prob.flux == 0 else "central", "stages": prob.stages,
             "precision": precision, "W": prob.W, "M": prob.M, "cfl": prob.cfl, "velocity": prob.vel_kind}
@@ -402,7 +408,7 @@ def run_ours(args):
     solver.close()
 
     if rank == 0:
-        launches_per_step = 2 if prob.stages == 2 else 3
+        launches_per_step = 3 if prob.stages == 3 else 2
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -418,7 +424,8 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": desc.get("kernel", "step_fast_kernel (TMA-staged fused two-stage DUGKS step)"
                                             if prob.stages == 2 else
-                                            "step_fast_kernel KIND_T3A + KIND_T3B (the two kernels of a three-stage step)"),
+                                            "step_fast_kernel KIND_T3A + KIND_T3B (the two kernels of a three-stage step)"
+                                            if prob.stages == 3 else "dvm_step_kernel (streaming-collision DVM)"),
                          "bytes_per_cell": bpc,
                          "bytes_per_cell_actual": BYTES_PER_CELL_ACTUAL[(args.precision, prob.stages)],
                          "peak_source": peak_kind, "avg_kernel_ms": avg_step_ms},
@@ -435,7 +442,8 @@ def run_ours(args):
                             also_single(args.workload, args.precision, 100, flush_l2=False),
                             also_single("slotted_disk256", "fp32", 300),
                             also_single(args.workload, "fp64", 20, generic=True),
-                            also_single("vortex1024_t3", "fp32", 50), also_single("vortex1024_p4", "fp32", 50)]
+                            also_single("vortex1024_t3", "fp32", 50), also_single("vortex1024_p4", "fp32", 50),
+                            also_single("vortex1024_dvm", "fp32", 50), also_single("vortex1024_lbm", "fp32", 50)]
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

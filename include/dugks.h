@@ -59,7 +59,12 @@ enum { DUGKS_VEL_UNIFORM = 0, DUGKS_VEL_ROTATION = 1, DUGKS_VEL_VORTEX = 2, DUGK
  *              upwind reconstruction Eq. (26); gradient order of Eq. (2).
  *   flux       DUGKS_UPWIND (Eq. (26)) or DUGKS_CENTRAL (Eq. (25)).
  *   stages     2: original two-stage DUGKS; 3: three-stage third-order DUGKS
- *              (Sec. II.B.2), which needs dt < 12 tau (Sec. III.A).
+ *              (Sec. II.B.2), which needs dt < 12 tau (Sec. III.A); 1: the
+ *              streaming-collision discrete velocity method of Sec. II.B.1
+ *              (Eqs. (8)-(14), the comparison scheme of the paper; flux unused,
+ *              order = the Taylor degree + 1 of the streaming interpolation
+ *              Eq. (12)), which at cfl = 1 is the lattice Boltzmann method
+ *              (FP64 and FP32 storage).
  *   precision  DUGKS_FP64, DUGKS_FP32, or DUGKS_FP16F (FP32 arithmetic; f stored
  *              in half precision as the scaled deviation f_k - w_k phi, phi kept
  *              in FP32; two-stage only). FP32 and FP16F keep phi as an FP32 plane
@@ -108,7 +113,10 @@ int dugks_set_velocity(dugks_ctx *c, int kind, const double *params, const doubl
  * bar f at x_b - xi h by Eqs. (24)-(26), the face phi, equilibrium, source
  * and original f of Eqs. (27)-(28), and the meso-flux update of Eq. (21), and
  * also writes per-tile FP64 mass partials. Three-stage (Eqs. (29)-(34)): two
- * kernels per step (steps (i)-(ii) and (iii)-(iv) of Sec. II.B.2). */
+ * kernels per step (steps (i)-(ii) and (iii)-(iv) of Sec. II.B.2). DVM
+ * (stages = 1): one kernel per step, streaming (Eqs. (11a), (12)), phi of
+ * Eq. (13), cell quantities at t + dt and the collision of Eq. (11b), with the
+ * same per-tile mass partials. */
 int dugks_step(dugks_ctx *c, int64_t nsteps);
 
 /* Waits for the stream and writes phi = sum_k f_k (Eq. (30)) into out_host

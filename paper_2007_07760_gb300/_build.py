@@ -12,7 +12,7 @@ LIB = os.path.join(HERE, "libdugks.so")
 SOURCES = ["dugks_api.cu", "dugks_noalloc.cu", "dugks_batch.cu"] + [
     f"dugks_inst_{p}_{k}.cu" for p in ("f64", "f32", "f16") for k in ("gen", "fast", "batch")] + [
     "dugks_inst_f64_t3.cu", "dugks_inst_f32_t3.cu", "dugks_inst_f64_o4.cu", "dugks_inst_f32_o4.cu",
-    "dugks_inst_f16_o4.cu"]
+    "dugks_inst_f16_o4.cu", "dugks_inst_dvm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

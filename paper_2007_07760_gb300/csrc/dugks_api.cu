@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/dugks.h"
+#include "dugks_dvm.cuh"
 #include "dugks_host.h"
 #include "dugks_internal.h"
 
@@ -84,7 +85,7 @@ int check_params(const dugks_params *p, std::string &why) {
     if (!(p->cfl > 0) || p->cfl > 1.0) { why = "cfl must be in (0, 1]"; return DUGKS_EINVAL; }
     if (p->order < 2 || p->order > 4) { why = "order must be 2, 3 or 4"; return DUGKS_EINVAL; }
     if (p->flux != DUGKS_UPWIND && p->flux != DUGKS_CENTRAL) { why = "flux must be upwind or central"; return DUGKS_EINVAL; }
-    if (p->stages != 2 && p->stages != 3) { why = "stages must be 2 or 3"; return DUGKS_EINVAL; }
+    if (p->stages < 1 || p->stages > 3) { why = "stages must be 1 (DVM), 2 or 3"; return DUGKS_EINVAL; }
     if (p->precision < DUGKS_FP64 || p->precision > DUGKS_FP16F) { why = "unknown precision"; return DUGKS_EINVAL; }
     if (p->precision == DUGKS_FP16F && p->stages != 2) { why = "FP16 storage is two-stage only"; return DUGKS_EINVAL; }
     if (!(p->phiA != p->phiB) || !std::isfinite(p->phiA) || !std::isfinite(p->phiB)) { why = "phiA must differ from phiB"; return DUGKS_EINVAL; }
@@ -153,7 +154,9 @@ template <typename T, typename ST>
 int run_init(dugks_ctx *c) {
     StepParams<T> q = base_params<T>(c);
     q.t = (T)0;
-    const double frac = c->p.stages == 2 ? 0.5 : 0.25;
+    // tilde f = f - (dt/2)(Omega + S), hat f = f - (dt/4)(Omega + S); the DVM's
+    // tilde f^+ = f + (dt/2)(Omega + S) (Eq. (9)); Omega = 0 at the start
+    const double frac = c->p.stages == 2 ? 0.5 : c->p.stages == 3 ? 0.25 : -0.5;
     if (Store<T, ST>::phi_plane) {
         c->pr[0] = 0; c->pr[1] = 1; c->pr[2] = 2;
     }
@@ -381,9 +384,45 @@ int step_t3(dugks_ctx *c) {
     return DUGKS_OK;
 }
 
+// One step of the streaming-collision DVM (Sec. II.B.1; the LBM at dt = 1):
+// X[cur] -> X[1-cur]. phi as a sum of X (FP64): phi[pr0] holds phi^n (of X),
+// phi[pr1] receives phi^{n+1}. phi as a plane of its own (FP32): phi[pr0] = phi^n,
+// phi[pr2] receives phi^{n+1}, the roles rotating as in step_t2.
+template <typename T>
+int step_dvm(dugks_ctx *c) {
+    constexpr bool PHIP = Store<T, T>::phi_plane;
+    StepParams<T> q = base_params<T>(c);
+    const double dt = c->p.cfl, tau = 3.0 * c->p.M, t = (double)c->step * dt;
+    q.t_old = (T)t;          // time of the state and of phi_old
+    q.t = (T)(t + dt);       // time of the new cell quantities
+    q.inv_dtD = (T)(1.0 / dt);
+    q.useD = c->p.dtphiu ? 1 : 0;
+    q.X = c->X[c->cur];
+    q.out1 = c->X[1 - c->cur];
+    q.mass_partial = c->partial;
+    q.phi_old = static_cast<const T *>(c->phi[c->pr[0]]);
+    q.phi_out = static_cast<T *>(c->phi[PHIP ? c->pr[2] : c->pr[1]]);
+    DvmExtra<T> dv;
+    dv.s = dt >= 0.5 ? 1 : 0;
+    dv.d = (T)(dv.s - dt);
+    dv.beta = (T)(2.0 * dt / (2.0 * tau + dt));
+    cudaError_t e = launch_dvm<T>(q, dv, c->p.order, dt == 1.0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "DVM kernel");
+    c->cur = 1 - c->cur;
+    if (PHIP) {
+        const int a0 = c->pr[0], a1 = c->pr[1], a2 = c->pr[2];
+        c->pr[0] = a2; c->pr[1] = a0; c->pr[2] = a1;
+    } else {
+        std::swap(c->pr[0], c->pr[1]);
+    }
+    return DUGKS_OK;
+}
+
 int step_once(dugks_ctx *c) {
     int r;
-    if (c->p.stages == 3) {
+    if (c->p.stages == 1) {
+        r = is_fp64(c) ? step_dvm<double>(c) : step_dvm<float>(c);
+    } else if (c->p.stages == 3) {
         r = is_fp64(c) ? step_t3<double>(c) : step_t3<float>(c);
     } else {
         switch (c->p.precision) {
@@ -556,7 +595,8 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     c->nphi = p->precision == DUGKS_FP64 ? 2 : p->stages == 3 ? 4 : 3;
     // the TMA-staged kernels serve every order and both schemes (three-stage: full
     // storage; order 4 and the three-stage scheme: one tile shape, 8 x 2)
-    c->fast = (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
+    // (the DVM has one kernel of its own)
+    c->fast = p->stages != 1 && (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
     if (c->fast && (p->stages == 3 || p->order == 4)) {
         c->variant = 2;
     } else if (c->fast) {
@@ -808,7 +848,8 @@ int dugks_selftest_fail_allocs(int32_t skip, int32_t count) {
 
 int dugks_set_variant(dugks_ctx *c, int variant) {
     if (!c || variant < -1 || variant >= FAST_VARIANTS) return DUGKS_EINVAL;
-    const bool fast_capable = (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) && encode_fn() != nullptr;
+    const bool fast_capable =
+        c->p.stages != 1 && (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) && encode_fn() != nullptr;
     if (!fast_capable) return DUGKS_OK;
     // order 4 and the three-stage kernels have one tile shape
     if ((c->p.stages == 3 || c->p.order == 4) && variant >= 0) variant = 2;

@@ -63,6 +63,13 @@ cudaError_t launch_batch_advance(BatchGrid<T> *grids, int ngrids, const double *
 
 cudaError_t launch_mass_final(const double *partial, int n, double *out, int *status, cudaStream_t s);
 
+// One step of the streaming-collision DVM (dugks_inst_dvm.cu); lbm: the plain
+// streaming of dt = 1 (T = double or float, full storage).
+template <typename T>
+struct DvmExtra;
+template <typename T>
+cudaError_t launch_dvm(const StepParams<T> &p, const DvmExtra<T> &dv, int order, bool lbm, cudaStream_t s);
+
 // Every device allocation of the library goes through dev_malloc: cudaMalloc
 // behind a host-side test hook (dugks_selftest_fail_allocs) that can make chosen
 // allocations report cudaErrorMemoryAllocation without touching the device.
