@@ -274,8 +274,11 @@ void orc_cell_quantities(const orc_params *p, const double *phi, const double *p
     const size_t N = (size_t)nx * ny;
     const double tau = p->M / RT;
     double *gx = malloc(N * sizeof(double)), *gy = malloc(N * sizeof(double));
-    orc_derivative(p->order, 0, phi, nx, ny, gx);
-    orc_derivative(p->order, 1, phi, nx, ny, gy);
+    /* Reading: the gradient of phi for n is the isotropic one of the order; DUGKS-T2S5,
+     * whose reconstruction is not an isotropic stencil, takes the fourth-order one */
+    const int gorder = p->order == 5 ? 4 : p->order;
+    orc_derivative(gorder, 0, phi, nx, ny, gx);
+    orc_derivative(gorder, 1, phi, nx, ny, gy);
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
@@ -344,7 +347,63 @@ static double taylor(const orc_params *p, const deriv_set *D, size_t c, double d
     return v;
 }
 
+/* Weight of node a (a = -2..2, unit spacing, centre 0) of the degree-4 Lagrange
+ * interpolant at offset s from the centre node. */
+static double lagrange5(int a, double s) {
+    double w = 1.0;
+    for (int b = -2; b <= 2; b++)
+        if (b != a) w *= (s - b) / (double)(a - b);
+    return w;
+}
+
+/* bar f^+ at q from the 5 x 5 cells centred at the cell (m, n): the tensor-product
+ * degree-4 interpolant (error O(dx^5), not isotropic). */
+static double interp5(const orc_params *p, const double *F, int m, int n, double qx, double qy) {
+    const double sx = qx - (m + 0.5), sy = qy - (n + 0.5);
+    double v = 0.0;
+    for (int b = -2; b <= 2; b++) {
+        double row = 0.0;
+        for (int a = -2; a <= 2; a++) row += lagrange5(a, sx) * F[idx(p, m + a, n + b)];
+        v += lagrange5(b, sy) * row;
+    }
+    return v;
+}
+
+/* DUGKS-T2S5 (Sec. III.A: fifth-order reconstruction, a stencil "not isotropic",
+ * no stencil printed). Reading: bar f^+ at the back-traced point q = x_b - xi h
+ * is the tensor-product degree-4 Lagrange interpolant on the 5 x 5 cells centred
+ * at the cell nearest to q (upwind-biased); on a face (xi normal to it zero) the
+ * two nearest cells tie and the two interpolants are averaged, as for Eq. (26);
+ * along the face q stays in the face's row. */
+static void reconstruct5(const orc_params *p, const double *fbp, double h, double *fbarE, double *fbarN) {
+    const int nx = p->nx, ny = p->ny;
+    const size_t N = (size_t)nx * ny;
+    for (int k = 0; k < Q; k++) {
+        const double *F = fbp + k * N;
+        const int ex = EX[k], ey = EY[k];
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                size_t c = (size_t)j * nx + i;
+                double qx = i + 1.0 - ex * h, qy = j + 0.5 - ey * h;   /* east face */
+                double vE = ex > 0 ? interp5(p, F, i, j, qx, qy)
+                          : ex < 0 ? interp5(p, F, i + 1, j, qx, qy)
+                                   : 0.5 * (interp5(p, F, i, j, qx, qy) + interp5(p, F, i + 1, j, qx, qy));
+                qx = i + 0.5 - ex * h; qy = j + 1.0 - ey * h;          /* north face */
+                double vN = ey > 0 ? interp5(p, F, i, j, qx, qy)
+                          : ey < 0 ? interp5(p, F, i, j + 1, qx, qy)
+                                   : 0.5 * (interp5(p, F, i, j, qx, qy) + interp5(p, F, i, j + 1, qx, qy));
+                fbarE[k * N + c] = vE;
+                fbarN[k * N + c] = vN;
+            }
+    }
+}
+
 void orc_reconstruct(const orc_params *p, const double *fbp, double h, double *fbarE, double *fbarN) {
+    if (p->order == 5) {
+        reconstruct5(p, fbp, h, fbarE, fbarN);
+        return;
+    }
     const int nx = p->nx, ny = p->ny;
     const size_t N = (size_t)nx * ny;
     double *buf = malloc(9 * N * sizeof(double));
@@ -448,8 +507,11 @@ void orc_flux(const orc_params *p, const double *fE, const double *fN, double *L
 int orc_check(const orc_params *p) {
     if (p->nx < 8 || p->ny < 8) return -1;
     if (!(p->W > 0) || !(p->M > 0) || !(p->cfl > 0) || p->cfl > 1.0) return -1;
-    if (p->order < 2 || p->order > 4 || (p->flux != 0 && p->flux != 1)) return -1;
+    if (p->order < 2 || p->order > 5 || (p->flux != 0 && p->flux != 1)) return -1;
+    /* order 5: DUGKS-T2S5 (Sec. III.A), the two-stage scheme with upwind faces */
+    if (p->order == 5 && (p->flux != 0 || p->stages != 2)) return -1;
     if (p->stages < 1 || p->stages > 3) return -1;   /* 1: streaming-collision DVM (Sec. II.B.1) */
+    if (p->stages == 1 && p->order > 4) return -1;
     if (p->phiA == p->phiB) return -1;
     if (p->vel_kind < 0 || p->vel_kind > 5) return -1;
     if (p->vel_kind == 5 && (p->vel[0] <= 0 || p->vel[2] <= 0)) return -1;

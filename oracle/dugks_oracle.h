@@ -26,7 +26,8 @@ typedef struct {
     double W;        /* interface width, Sec. II.A */
     double M;        /* mobility; relaxation time tau = M / RT = 3 M */
     double cfl;      /* CFL number C; dt = C dx / sqrt(3 RT) = C, Eq. (39) */
-    int order;       /* 2, 3 or 4 */
+    int order;       /* 2, 3 or 4; 5 = DUGKS-T2S5 (fifth-order upwind reconstruction,
+                        two-stage, upwind only) */
     int flux;        /* 0 = upwind Eq. (26), 1 = central Eq. (25) */
     int stages;      /* 2 = original DUGKS, 3 = three-stage third-order DUGKS,
                         1 = streaming-collision DVM (Sec. II.B.1; flux unused) */

@@ -1,4 +1,5 @@
-"""Pins of the oracle's face reconstruction (Eqs. (24)-(26), Sec. II.B.2).
+"""Pins of the oracle's face reconstruction (Eqs. (24)-(26), Sec. II.B.2), and of the
+fifth-order reconstruction of DUGKS-T2S5 (Sec. III.A) against numpy's polynomial fit.
 
 An independent per-face routine finds the cell centre nearest to the
 back-traced point x_b - xi h by explicit geometric search (ties averaged), and
@@ -143,3 +144,90 @@ def test_face_value_order_on_smooth_data(oracle):
     # order 4: at least fourth order (its fifth-order terms still dominate here)
     assert np.log2(errs[4][0] / errs[4][1]) > 3.8
     assert errs[4][1] < errs[3][1] < errs[2][1]
+
+
+# ---- order 5: DUGKS-T2S5 (Sec. III.A: fifth-order, not isotropic; no stencil printed) ----
+def _interp_polyfit(F, m, n, qx, qy):
+    """Degree-4 interpolant through the 5 x 5 cells around cell (m, n), evaluated at
+    q: numpy's polynomial fit row by row, then across the rows (an independent
+    construction of the same tensor-product interpolant)."""
+    ny, nx = F.shape
+    xs = np.arange(m - 2, m + 3) + 0.5
+    ys = np.arange(n - 2, n + 3) + 0.5
+    rows = []
+    for y in range(n - 2, n + 3):
+        vals = [F[y % ny, x % nx] for x in range(m - 2, m + 3)]
+        rows.append(np.polyval(np.polyfit(xs - qx, vals, 4), 0.0))
+    return np.polyval(np.polyfit(ys - qy, rows, 4), 0.0)
+
+
+def _brute5(fbp, h):
+    _, ny, nx = fbp.shape
+    outE, outN = np.zeros_like(fbp), np.zeros_like(fbp)
+    for k in range(9):
+        F = fbp[k]
+        for j in range(ny):
+            for i in range(nx):
+                for (xb, yb), out, face in (((i + 1.0, j + 0.5), outE, 0), ((i + 0.5, j + 1.0), outN, 1)):
+                    qx, qy = xb - EX[k] * h, yb - EY[k] * h
+                    # the cell centres nearest to q along the face normal (both on a tie);
+                    # along the face q stays in the face's row or column
+                    if face == 0:
+                        d = [abs(qx - (c + 0.5)) for c in (i, i + 1)]
+                        cells = [(c, j) for c, dc in zip((i, i + 1), d) if dc <= min(d) + 1e-12]
+                    else:
+                        d = [abs(qy - (c + 0.5)) for c in (j, j + 1)]
+                        cells = [(i, c) for c, dc in zip((j, j + 1), d) if dc <= min(d) + 1e-12]
+                    out[k, j, i] = np.mean([_interp_polyfit(F, m, n, qx, qy) for m, n in cells])
+    return outE, outN
+
+
+@pytest.mark.parametrize("h", [0.4, 0.25, 0.5, 1 / 12])
+def test_order5_faces_match_brute_force(oracle, h):
+    rng = np.random.default_rng(51)
+    p = oracle.Params(10, 9, order=5, flux=0)
+    fbp = rng.standard_normal((9, 9, 10))
+    E, N = oracle.reconstruct(p, fbp, h)
+    bE, bN = _brute5(fbp, h)
+    assert np.abs(E - bE).max() < 1e-11
+    assert np.abs(N - bN).max() < 1e-11
+
+
+def test_order5_reproduces_degree_four_in_each_variable(oracle):
+    n = 24
+    x = np.arange(n) + 0.5
+    X, Y = np.meshgrid(x, x)
+    rng = np.random.default_rng(52)
+    coef = rng.standard_normal((5, 5)) * 0.1
+
+    def poly(px, py):
+        return sum(coef[a, b] * ((px - 12) / 4) ** a * ((py - 12) / 4) ** b for a in range(5) for b in range(5))
+
+    fbp = np.stack([poly(X, Y)] * 9)
+    h = 0.3
+    E, N = oracle.reconstruct(oracle.Params(n, n, order=5, flux=0), fbp, h)
+    for k in range(9):
+        for j in range(6, 18):
+            for i in range(6, 18):
+                assert E[k, j, i] == pytest.approx(poly(i + 1.0 - EX[k] * h, j + 0.5 - EY[k] * h), abs=1e-10)
+                assert N[k, j, i] == pytest.approx(poly(i + 0.5 - EX[k] * h, j + 1.0 - EY[k] * h), abs=1e-10)
+
+
+def test_order5_face_values_converge_at_fifth_order(oracle):
+    errs = []
+    for n in (32, 64):
+        x = np.arange(n) + 0.5
+        X, Y = np.meshgrid(x, x)
+        k = 2 * np.pi / n
+        fbp = np.stack([np.sin(k * (X + 2 * Y))] * 9)
+        h = 0.3
+        E, _ = oracle.reconstruct(oracle.Params(n, n, order=5, flux=0), fbp, h)
+        ex = np.stack([np.sin(k * ((X + 0.5 - EX[q] * h) + 2 * (Y - EY[q] * h))) for q in range(9)])
+        errs.append(np.abs(E - ex).max())
+    assert abs(np.log2(errs[0] / errs[1]) - 5) < 0.3, errs
+
+
+def test_order5_only_upwind_two_stage(oracle):
+    assert oracle.check(oracle.Params(16, 16, order=5, flux=0, stages=2))
+    assert not oracle.check(oracle.Params(16, 16, order=5, flux=1, stages=2))
+    assert not oracle.check(oracle.Params(16, 16, order=5, flux=0, stages=3, cfl=0.5, M=0.02))
