@@ -56,7 +56,12 @@ enum { DUGKS_VEL_UNIFORM = 0, DUGKS_VEL_ROTATION = 1, DUGKS_VEL_VORTEX = 2, DUGK
  *   M > 0      mobility of Eq. (1); tau = 3 M.
  *   cfl        in (0, 1]; dt = cfl.
  *   order      2, 3 or 4: derivative stencils and Taylor degree order - 1 of the
- *              upwind reconstruction Eq. (26); gradient order of Eq. (2).
+ *              upwind reconstruction Eq. (26); gradient order of Eq. (2). 5:
+ *              DUGKS-T2S5 (Sec. III.A), the fifth-order reconstruction: the
+ *              degree-4 tensor-product Lagrange interpolant on the 5 x 5 cells
+ *              centred at the cell nearest to x_b - xi h (the paper prints no
+ *              stencil), the gradient of order 4; upwind, two-stage, TMA-staged
+ *              kernels only (dugks_set_variant(-1) and dugks_debug_faces refuse it).
  *   flux       DUGKS_UPWIND (Eq. (26)) or DUGKS_CENTRAL (Eq. (25)).
  *   stages     2: original two-stage DUGKS; 3: three-stage third-order DUGKS
  *              (Sec. II.B.2), which needs dt < 12 tau (Sec. III.A); 1: the

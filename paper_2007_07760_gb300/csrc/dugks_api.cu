@@ -83,7 +83,11 @@ int check_params(const dugks_params *p, std::string &why) {
     if ((int64_t)(p->nx + 2 * GHOST + 32) * (p->ny + 2 * GHOST) > (int64_t)1 << 31) { why = "grid too large"; return DUGKS_EINVAL; }
     if (!(p->W > 0) || !(p->M > 0)) { why = "W and M must be > 0"; return DUGKS_EINVAL; }
     if (!(p->cfl > 0) || p->cfl > 1.0) { why = "cfl must be in (0, 1]"; return DUGKS_EINVAL; }
-    if (p->order < 2 || p->order > 4) { why = "order must be 2, 3 or 4"; return DUGKS_EINVAL; }
+    if (p->order < 2 || p->order > 5) { why = "order must be 2, 3, 4 or 5"; return DUGKS_EINVAL; }
+    if (p->order == 5 && (p->flux != DUGKS_UPWIND || p->stages != 2)) {
+        why = "order 5 (DUGKS-T2S5) is two-stage with upwind faces";
+        return DUGKS_EINVAL;
+    }
     if (p->flux != DUGKS_UPWIND && p->flux != DUGKS_CENTRAL) { why = "flux must be upwind or central"; return DUGKS_EINVAL; }
     if (p->stages < 1 || p->stages > 3) { why = "stages must be 1 (DVM), 2 or 3"; return DUGKS_EINVAL; }
     if (p->precision < DUGKS_FP64 || p->precision > DUGKS_FP16F) { why = "unknown precision"; return DUGKS_EINVAL; }
@@ -163,7 +167,9 @@ int run_init(dugks_ctx *c) {
     q.out1 = c->p.stages == 3 ? c->X[0] : c->X[c->cur];
     // a phi plane: phi of the state; otherwise phi0 as the previous level
     q.phi_out = static_cast<T *>(c->phi[c->pr[0]]);
-    cudaError_t e = Launch<T, ST>::init(q, static_cast<const T *>(c->phi0), (T)(frac * c->p.cfl), c->p.order, c->stream);
+    // (the initial source takes the gradient of the order; order 5 has the fourth-order one)
+    cudaError_t e = Launch<T, ST>::init(q, static_cast<const T *>(c->phi0), (T)(frac * c->p.cfl),
+                                        c->p.order == 5 ? 4 : c->p.order, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "init kernel");
     c->initialized = true;
     c->mass_valid = false;
@@ -238,9 +244,10 @@ int step_t2(dugks_ctx *c, double *dbg = nullptr) {
         e = Launch<T, ST>::step(q, c->p.order, c->p.flux, KIND_T2, c->stream);
         return e == cudaSuccess ? DUGKS_OK : cuda_fail(c, e, "debug step kernel");
     }
-    if (c->fast && c->p.order == 4) {
+    if (c->fast && c->p.order >= 4) {
         if (c->coef_h != h) {
-            const FaceCoefs<T, 2> cf = make_face_coefs_r<T, 2>(4, c->p.flux, h);
+            // (order 4: the Taylor stencils; order 5: the Lagrange ones)
+            const FaceCoefs<T, 2> cf = make_face_coefs_r<T, 2>(c->p.order, c->p.flux, h);
             c->coefs.assign(reinterpret_cast<const unsigned char *>(&cf),
                             reinterpret_cast<const unsigned char *>(&cf) + sizeof cf);
             c->coef_h = h;
@@ -259,6 +266,7 @@ int step_t2(dugks_ctx *c, double *dbg = nullptr) {
         e = Launch<T, ST>::step_fast(q, cf, fx, c->tmX[c->cur], c->tmPhi[iPo], c->tmPhi[iPc], c->p.order,
                                      c->p.flux, c->variant, c->stream);
     } else {
+        if (c->p.order == 5) return fail(c, DUGKS_EINVAL, "order 5 needs the TMA-staged kernels");
         e = Launch<T, ST>::step(q, c->p.order, c->p.flux, KIND_T2, c->stream);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "step kernel");
@@ -330,7 +338,7 @@ int step_t3(dugks_ctx *c) {
         }
         c->coef3_dt = dt;
     }
-    if (c->fast && c->p.order == 4) {
+    if (c->fast && c->p.order >= 4) {
         e = Launch<T, T>::step_fast4(A, *reinterpret_cast<const FaceCoefs<T, 2> *>(c->coefs3[0].data()),
                                      vortex_factors<T>(c, t, t - dt, t + dt / 6.0), c->tmX[0], c->tmPhi[aPo],
                                      c->tmPhi[aPc], c->p.flux, KIND_T3A, c->stream);
@@ -368,7 +376,7 @@ int step_t3(dugks_ctx *c) {
         B.phi_out = static_cast<T *>(c->phi[c->pr[1]]);
     }
     B.mass_partial = c->partial;
-    if (c->fast && c->p.order == 4) {
+    if (c->fast && c->p.order >= 4) {
         e = Launch<T, T>::step_fast4(B, *reinterpret_cast<const FaceCoefs<T, 2> *>(c->coefs3[1].data()),
                                      vortex_factors<T>(c, t + dt / 3.0, t, t + 0.75 * dt), c->tmX[1],
                                      c->tmPhi[bPo], c->tmPhi[bPc], c->p.flux, KIND_T3B, c->stream);
@@ -597,7 +605,7 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     // storage; order 4 and the three-stage scheme: one tile shape, 8 x 2)
     // (the DVM has one kernel of its own)
     c->fast = p->stages != 1 && (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
-    if (c->fast && (p->stages == 3 || p->order == 4)) {
+    if (c->fast && (p->stages == 3 || p->order >= 4)) {
         c->variant = 2;
     } else if (c->fast) {
         // measured (FP32, L2 flushed between steps): 8 warps x 2 rows per thread fastest
@@ -752,8 +760,8 @@ int dugks_debug_faces(dugks_ctx *c, double *fbar_E, double *fbar_N, double *f_E,
     // (argument errors leave the context usable: they are not sticky)
     if (!c || !fbar_E || !fbar_N || !f_E || !f_N) return DUGKS_EINVAL;
     if (c->sticky != DUGKS_OK) return c->sticky;
-    if (c->p.stages != 2) {
-        c->err = "face read-out serves the two-stage scheme";
+    if (c->p.stages != 2 || c->p.order == 5) {
+        c->err = "face read-out serves the two-stage scheme at orders 2-4";
         return DUGKS_EINVAL;
     }
     cudaSetDevice(c->dev);
@@ -852,7 +860,9 @@ int dugks_set_variant(dugks_ctx *c, int variant) {
         c->p.stages != 1 && (c->p.stages == 2 || c->p.precision != DUGKS_FP16F) && encode_fn() != nullptr;
     if (!fast_capable) return DUGKS_OK;
     // order 4 and the three-stage kernels have one tile shape
-    if ((c->p.stages == 3 || c->p.order == 4) && variant >= 0) variant = 2;
+    if ((c->p.stages == 3 || c->p.order >= 4) && variant >= 0) variant = 2;
+    // order 5 exists on the TMA-staged path only
+    if (c->p.order == 5 && variant < 0) return DUGKS_EINVAL;
     cudaSetDevice(c->dev);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");

@@ -77,7 +77,7 @@ inline double taylor_w(int order, double dx, double dy, int a, int b) {
     return w;
 }
 
-// Face-stencil tables for stencil radius R (1: orders 2-3, 2: order 4).
+// Face-stencil tables for stencil radius R (1: orders 2-3, 2: orders 4 and 5).
 template <typename T, int R>
 inline FaceCoefs<T, R> make_face_coefs_r(int order, int flux, double h) {
     constexpr int NE = 2 * R + 1, NA = 2 * R + 2;
@@ -95,7 +95,30 @@ inline FaceCoefs<T, R> make_face_coefs_r(int order, int flux, double h) {
             for (int b = -R; b <= R; b++)
                 for (int a = -R; a <= R; a++) n[k][cy + b + R][a + R] += wgt * taylor_w(order, dx, dy, a, b);
         };
-        if (flux == DUGKS_UPWIND) {
+        if (order == 5) {
+            // DUGKS-T2S5: the degree-4 tensor-product Lagrange interpolant on the 5 x 5
+            // cells centred at the cell nearest to x_b - xi h (ties averaged); R = 2
+            auto L5 = [](int a, double sd) {
+                double w = 1.0;
+                for (int b = -2; b <= 2; b++)
+                    if (b != a) w *= (sd - b) / (double)(a - b);
+                return w;
+            };
+            auto lagE = [&](int cx, double wgt, double sx, double sy) {   // centred at cell (cx, 0)
+                for (int b = -2; b <= 2; b++)
+                    for (int a = -2; a <= 2; a++) e[k][b + R][cx + a + R] += wgt * L5(a, sx) * L5(b, sy);
+            };
+            auto lagN = [&](int cy, double wgt, double sx, double sy) {   // centred at cell (0, cy)
+                for (int b = -2; b <= 2; b++)
+                    for (int a = -2; a <= 2; a++) n[k][cy + b + R][a + R] += wgt * L5(a, sx) * L5(b, sy);
+            };
+            if (kx > 0) lagE(0, 1.0, 0.5 - h, -ky * h);
+            else if (kx < 0) lagE(1, 1.0, h - 0.5, -ky * h);
+            else { lagE(0, 0.5, 0.5, -ky * h); lagE(1, 0.5, -0.5, -ky * h); }
+            if (ky > 0) lagN(0, 1.0, -kx * h, 0.5 - h);
+            else if (ky < 0) lagN(1, 1.0, -kx * h, h - 0.5);
+            else { lagN(0, 0.5, -kx * h, 0.5); lagN(1, 0.5, -kx * h, -0.5); }
+        } else if (flux == DUGKS_UPWIND) {
             if (kx > 0) addE(0, 1.0, 0.5 - h, -ky * h);
             else if (kx < 0) addE(1, 1.0, h - 0.5, -ky * h);
             else { addE(0, 0.5, 0.5, -ky * h); addE(1, 0.5, -0.5, -ky * h); }

@@ -91,7 +91,7 @@ static FastGeom geom_t() {
 
 template <typename T, typename ST>
 FastGeom Launch<T, ST>::fast_geom(int variant, int order) {
-    if (order == 4) {   // one tile shape for radius-2 stencils
+    if (order >= 4) {   // one tile shape for radius-2 stencils (orders 4 and 5)
         using FT = FastTile<T, ST, 8, 2, 2>;
         return FastGeom{FT::NT, FT::TX, FT::TY, FT::BW, FT::RH, FT::BWT};
     }

@@ -13,7 +13,7 @@ from paper_2007_07760_gb300 import workloads as WL
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "translation_e_phi.json")
 GOLDEN_EXT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "extension_e_phi.json")
-SCHEMES = {"T2S2CD": (2, 1, 2), "T2S3": (3, 0, 2), "T3S3": (3, 0, 3)}   # order, flux, stages
+SCHEMES = {"T2S2CD": (2, 1, 2), "T2S3": (3, 0, 2), "T3S3": (3, 0, 3), "T2S5": (5, 0, 2)}   # order, flux, stages
 
 
 def paper_value(scheme: str, cfl: float, n: int) -> float:
@@ -31,11 +31,12 @@ def e_phi(phi: np.ndarray, phi0: np.ndarray) -> float:
     return float(np.sqrt(((phi - phi0) ** 2).sum() / (phi0 ** 2).sum()))
 
 
-def extension_entries():
-    """Every printed DUGKS entry of the extension table: (scheme, cfl, Pe, E_phi)."""
+def extension_entries(schemes=("T2S2CD", "T2S3", "T3S3")):
+    """The printed DUGKS entries of the extension table of the given schemes:
+    (scheme, cfl, Pe, E_phi)."""
     t = json.load(open(GOLDEN_EXT))
-    return [(sch, float(c), pe, row[i]) for sch, rows in t["E_phi"].items() for c, row in rows.items()
-            for i, pe in enumerate(t["Pe"])]
+    return [(sch, float(c), pe, row[i]) for sch, rows in t["E_phi"].items() if sch in schemes
+            for c, row in rows.items() for i, pe in enumerate(t["Pe"])]
 
 
 def sweep_entries(which: str):

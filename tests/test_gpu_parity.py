@@ -194,7 +194,7 @@ def test_deterministic_and_checkpoint_resume():
 def test_invalid_parameters_rejected():
     phi0 = np.zeros((16, 16))
     bad = [dict(stages=3, cfl=0.8, M=0.02),          # dt >= 12 tau
-           dict(order=5), dict(cfl=1.5), dict(W=-1.0),
+           dict(order=6), dict(order=5, flux=1), dict(cfl=1.5), dict(W=-1.0),
            dict(precision="fp16f", stages=3, cfl=0.1, M=0.02)]
     for kw in bad:
         with pytest.raises(N.DugksError) as e:
