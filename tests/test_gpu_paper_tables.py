@@ -37,6 +37,7 @@ Zalesak at 0.87 to 1.02 of the printed values, the deformation at 0.62 (Pe 512) 
 1.05 (it is less dissipative than the paper's at low Pe), compared within 40%;
 and it is the least dissipative DUGKS scheme, as in the paper. Printed values:
 tests/golden/zalesak_e_phi.json, tests/golden/deformation_e_phi.json."""
+import functools
 import json
 import os
 
@@ -52,6 +53,7 @@ pytestmark = pytest.mark.gpu
 SCHEMES = [("T2S2CD", 0.8), ("T2S3", 0.8), ("T2S3", 0.5), ("T3S3", 0.5)]
 
 
+@functools.lru_cache(maxsize=None)   # (the trend tests reuse the table runs)
 def _run(scheme, cfl, n, precision):
     prob = problem(scheme, cfl, n)
     with N.Solver.from_problem(prob, precision=precision) as s:
@@ -128,6 +130,7 @@ SWEEP_TOL = {"zalesak": 0.15, "deformation": 0.06}
 FULL = os.environ.get("DUGKS_FULL_TABLES") == "1"
 
 
+@functools.lru_cache(maxsize=None)
 def _sweep_run(which, scheme, cfl, Pe, M):
     prob = sweep_problem(which, scheme, cfl, Pe, M)
     with N.Solver.from_problem(prob, precision="fp32") as s:
