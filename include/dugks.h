@@ -41,7 +41,8 @@ typedef enum {
     DUGKS_ECUDA = 3,       /* CUDA runtime error (message in dugks_last_error) */
     DUGKS_ETIMEOUT = 4,    /* a bounded device wait ran out */
     DUGKS_ENONFINITE = 5,  /* the field holds NaN or Inf */
-    DUGKS_ESTATE = 6       /* call not valid in the context's current state */
+    DUGKS_ESTATE = 6,      /* call not valid in the context's current state */
+    DUGKS_EAGAIN = 7       /* the result is not ready yet: call again later */
 } dugks_status_code;
 
 enum { DUGKS_FP64 = 0, DUGKS_FP32 = 1, DUGKS_FP16F = 2 };
@@ -212,7 +213,18 @@ void dugks_destroy(dugks_ctx *c);
  * counter on the device, so grids may join (dugks_batch_add) and leave
  * (dugks_batch_remove) between calls of dugks_batch_step, and a sequence of
  * steps is replayed as a CUDA graph. Every grid's result is bitwise the same
- * whatever else is in the batch. Two-stage scheme, orders 2 and 3 only. */
+ * whatever else is in the batch. Two-stage scheme, orders 2 and 3 only.
+ *
+ * Add, step, retire, collect (without wait), fence, reached and remove queue
+ * their device work on the batch's stream and return without waiting for it:
+ * grid memory comes from a stream-ordered memory pool owned by the batch, host
+ * data moves through pinned staging buffers, and whatever the stream may still
+ * read is released only after it has passed. A server can therefore admit and
+ * finish grids while earlier steps are still running; several batches on
+ * streams of different priority share the GPU tile by tile when their kernels
+ * run one CTA per tile (dugks_batch_set_ctas). The calls described as waiting
+ * (read_phi, mass, status, set_variant, destroy) synchronise the stream. A
+ * batch is not thread-safe: one host thread drives it. */
 typedef struct dugks_batch dugks_batch;
 
 /* Common parameters of all grids (nx, ny ignored; stages must be 2, order 2 or
@@ -224,14 +236,48 @@ size_t dugks_batch_grid_bytes(const dugks_params *common, int32_t nx, int32_t ny
 
 /* Adds a grid: phi0_host (ny * nx doubles), velocity kind UNIFORM, ROTATION or
  * VORTEX with its parameters (as dugks_set_velocity), and the number of steps
- * after which the grid stops advancing (target_steps < 0: unbounded). Builds
- * the initial equilibrium. *grid_id receives a non-negative id. DUGKS_ENOMEM
- * if the device memory is not available. */
+ * after which the grid stops advancing (target_steps < 0: unbounded). Queues
+ * the initial equilibrium on the stream (no wait). *grid_id receives a
+ * non-negative id. DUGKS_ENONFINITE (not sticky) for a field holding NaN or
+ * Inf; DUGKS_ENOMEM (not sticky) if device or pinned host memory is not
+ * available. */
 int dugks_batch_add(dugks_batch *b, int32_t nx, int32_t ny, const double *phi0_host, int vel_kind,
                     const double *vel_params, int64_t target_steps, int32_t *grid_id);
 
-/* Removes a grid and frees its device memory (waits for the stream). */
+/* Removes a grid: its device memory goes back to the batch's pool once the
+ * steps queued before the call have run (no wait). A pending read-out of a
+ * retiring grid is dropped. DUGKS_EINVAL for an unknown id. */
 int dugks_batch_remove(dugks_batch *b, int32_t grid_id);
+
+/* Finishing a grid without waiting. Freezes the grid where it stands (after the
+ * steps already queued), queues the read-out of phi (ny * nx doubles, widened to
+ * FP64 on the device) into a pinned host buffer owned by the batch, and returns
+ * in *ticket the fence that follows the copy. The grid leaves the work list; its
+ * id stays reserved until dugks_batch_collect or dugks_batch_remove. DUGKS_EINVAL
+ * for an unknown or already retiring id; DUGKS_ENOMEM (not sticky) if no pinned
+ * host memory is available. */
+int dugks_batch_retire(dugks_batch *b, int32_t grid_id, uint64_t *ticket);
+
+/* Result of a retired grid: if its read-out has completed (or wait != 0, after
+ * waiting for it) copies phi into out_host (ny * nx doubles, row-major), frees
+ * the grid as dugks_batch_remove does and returns DUGKS_OK. With wait == 0 and
+ * the copy still in flight it returns DUGKS_EAGAIN and changes nothing.
+ * DUGKS_EINVAL for an id that is not retiring. */
+int dugks_batch_collect(dugks_batch *b, int32_t grid_id, double *out_host, int wait);
+
+/* Fences: dugks_batch_fence records a point in the batch's stream and returns its
+ * ticket (tickets increase by one per fence, retire's included); dugks_batch_reached
+ * sets *done to 1 once the stream has passed it, else 0 (no wait). A caller
+ * keeps the number of steps in flight bounded with them. DUGKS_EINVAL for a
+ * ticket never issued. */
+int dugks_batch_fence(dugks_batch *b, uint64_t *ticket);
+int dugks_batch_reached(dugks_batch *b, uint64_t ticket, int32_t *done);
+
+/* CTAs of the step kernel: 0 (default) as many as are resident on the GPU, each
+ * striding over the work list; a negative value one CTA per tile, so that a
+ * kernel of a higher-priority stream takes SMs as soon as tiles finish; a
+ * positive value at most that many. DUGKS_EINVAL for a null batch. */
+int dugks_batch_set_ctas(dugks_batch *b, int32_t ctas);
 
 /* Enqueues nsteps steps of every grid that has not reached its target. */
 int dugks_batch_step(dugks_batch *b, int64_t nsteps);

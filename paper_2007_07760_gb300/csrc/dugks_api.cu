@@ -510,16 +510,31 @@ namespace dugks {
 // after them fail
 static std::atomic<int> g_alloc_skip{0}, g_alloc_fail{0};
 
-cudaError_t dev_malloc_raw(void **p, size_t bytes) {
+static bool alloc_hook_fails() {
     if (g_alloc_fail.load(std::memory_order_relaxed) > 0) {
         if (g_alloc_skip.fetch_sub(1, std::memory_order_relaxed) <= 0) {
             g_alloc_skip.store(0, std::memory_order_relaxed);
             g_alloc_fail.fetch_sub(1, std::memory_order_relaxed);
-            *p = nullptr;
-            return cudaErrorMemoryAllocation;
+            return true;
         }
     }
+    return false;
+}
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes) {
+    if (alloc_hook_fails()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_pool(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t s) {
+    if (alloc_hook_fails()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 // Fixed-order sum of the per-tile partials (deterministic); flags NaN / Inf.

@@ -62,80 +62,6 @@ __host__ __device__ constexpr bool tapN(int flux, int k, int b, int a, int R = 1
                                    : (R > 1 || a != 0 || b == 0 || b == 1));
 }
 
-// ---- shared face-stencil values (radius 1: orders 2 and 3) -----------------------
-// The 252 radius-1 face-stencil coefficients of a step take only 25 distinct values
-// (upwind) or 5 (central): the mirror symmetries of the Taylor expansion of Eq. (26)
-// (x -> -x together with the expansion cell, y -> -y, the tie average, and the
-// exchange of x and y between east and north faces) and of the central form of
-// Eq. (25). fast_tile reads every tap through a representative entry of the table,
-// so a kernel reads 25 (or 5) distinct parameters instead of 252 and can keep them
-// in uniform registers.
-// Index (and sign) in the list of distinct values of the east-face tap at row b
-// (-1..1) and column a (-1..2), offsets from the face-owner cell, of a direction
-// with lattice velocity (kx, ky).
-//  Upwind (Eq. (26)): the expansion about the cell on the kx side mirrors to kx > 0
-//  (column a -> 1 - a), ky < 0 mirrors to ky > 0 (row b -> -b); the tie (kx = 0)
-//  averages two mirror-image expansions (a -> 1 - a leaves it unchanged) and a
-//  stencil with ky = 0 is even in b. Four canonical blocks remain:
-//    (kx, ky) = (1, 0): a -1..1, b 0..1  -> 0..5
-//               (1, 1): a -1..1, b -1..1 -> 6..14
-//               (0, 0): a -1..0, b 0..1  -> 15..18
-//               (0, 1): a -1..0, b -1..1 -> 19..24
-//  Central (Eq. (25)): (b, a) = (0, 0) -> 1/2 + h kx, (0, 1) -> 1/2 - h kx
-//  (indices 0..2 hold 1/2 - h, 1/2, 1/2 + h); b != 0 (ky != 0): the tangential
-//  derivative, sign -ky b times h/24 (a = -1, 2; index 3) or 5h/24 (a = 0, 1; 4).
-struct TapIdx {
-    int i, s;
-};
-__host__ __device__ constexpr TapIdx tap_idx_e(int flux, int kx, int ky, int b, int a) {
-    if (flux == 0) {
-        if (kx < 0) {
-            kx = 1;
-            a = 1 - a;
-        }
-        if (ky < 0) {
-            ky = 1;
-            b = -b;
-        }
-        if (kx == 0 && a >= 1) a = 1 - a;
-        if (ky == 0 && b < 0) b = -b;
-        if (kx == 1 && ky == 0) return TapIdx{(a + 1) * 2 + b, 1};
-        if (kx == 1) return TapIdx{6 + (a + 1) * 3 + (b + 1), 1};
-        if (ky == 0) return TapIdx{15 + (a + 1) * 2 + b, 1};
-        return TapIdx{19 + (a + 1) * 3 + (b + 1), 1};
-    }
-    if (b == 0) return TapIdx{a == 0 ? 1 + kx : 1 - kx, 1};
-    return TapIdx{(a == 0 || a == 1) ? 4 : 3, -ky * b};
-}
-// north-face tap at row b (-1..2), column a (-1..1): the east face of the
-// direction with x and y exchanged (both Eq. (25) and Eq. (26) are symmetric
-// under that exchange)
-__host__ __device__ constexpr TapIdx tap_idx_n(int flux, int kx, int ky, int b, int a) {
-    return tap_idx_e(flux, ky, kx, a, b);
-}
-// A representative east-face tap (direction k0, row b0, column a0, sign s0) of
-// every canonical index: FaceCoefs::e[k0][b0 + 1][a0 + 1] = s0 * (value at i).
-struct TapRep {
-    int k, b, a, s;
-};
-__host__ __device__ constexpr TapRep tap_rep(int flux, int i) {
-    if (flux == 0) {
-        if (i < 6) return TapRep{1, i % 2, i / 2 - 1, 1};              // (kx, ky) = (1, 0)
-        if (i < 15) return TapRep{2, (i - 6) % 3 - 1, (i - 6) / 3 - 1, 1};   // (1, 1)
-        if (i < 19) return TapRep{0, (i - 15) % 2, (i - 15) / 2 - 1, 1};     // (0, 0)
-        return TapRep{3, (i - 19) % 3 - 1, (i - 19) / 3 - 1, 1};              // (0, 1)
-    }
-    if (i < 3) return TapRep{i == 0 ? 5 : i == 1 ? 0 : 1, 0, 0, 1};   // 1/2 - h, 1/2, 1/2 + h
-    return TapRep{3, 1, i == 3 ? -1 : 0, -1};                          // -h/24, -5h/24 at (b, a) = (1, -1), (1, 0)
-}
-
-// taps whose value is zero for every h: order 2 (linear Taylor) of an upwind
-// face whose back-traced point lies on the expansion cell's row has no weight
-// on the rest of that cell's column (the gradient's x-stencil vanishes there)
-__host__ __device__ constexpr bool tap_zero(int order, int flux, TapIdx w) {
-    return order == 2 && flux == 0 && w.i == 3;
-}
-
 // Per-step scalars of the fast kernel that the generic parameters do not carry.
 template <typename T>
 struct FastExtra {
@@ -598,30 +524,12 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             for (int b = 0; b < 2 * R + 1; b++)
 #pragma unroll
                 for (int a = 0; a < 2 * R + 2; a++)
-                    if (tapE(FLUX, k, b - R, a - R, R)) {
-                        if constexpr (R == 1) {   // through the tap's representative (shared value)
-                            const TapIdx w = tap_idx_e(FLUX, kx, ky, b - 1, a - 1);
-                            const TapRep q = tap_rep(FLUX, w.i);
-                            if (!tap_zero(ORDER, FLUX, w))
-                                se += T(w.s * q.s) * cf.e[q.k][q.b + 1][q.a + 1] * win[r + b][a];
-                        } else {
-                            se += cf.e[k][b][a] * win[r + b][a];
-                        }
-                    }
+                    if (tapE(FLUX, k, b - R, a - R, R)) se += cf.e[k][b][a] * win[r + b][a];
 #pragma unroll
             for (int b = 0; b < 2 * R + 2; b++)
 #pragma unroll
                 for (int a = 0; a < 2 * R + 1; a++)
-                    if (tapN(FLUX, k, b - R, a - R, R)) {
-                        if constexpr (R == 1) {
-                            const TapIdx w = tap_idx_n(FLUX, kx, ky, b - 1, a - 1);
-                            const TapRep q = tap_rep(FLUX, w.i);
-                            if (!tap_zero(ORDER, FLUX, w))
-                                sn += T(w.s * q.s) * cf.e[q.k][q.b + 1][q.a + 1] * win[r + b][a];
-                        } else {
-                            sn += cf.n[k][b][a] * win[r + b][a];
-                        }
-                    }
+                    if (tapN(FLUX, k, b - R, a - R, R)) sn += cf.n[k][b][a] * win[r + b][a];
             fe[r] = se;
             fn[r] = sn;
             phbE[r] += se;
@@ -864,7 +772,20 @@ struct alignas(64) BatchGrid {
     int item0, nitems;       // its tiles in the work list
     int vel_kind, pad_;
     double vp[3];            // velocity parameters (FP64; rounded per precision in the kernel)
+    T vc[3];                 // single vortex: cos(pi t / T) at t, t - dt, t + dt/2 of the current step
 };
+
+// Reversal factors of a vortex grid for its current step, in FP64 (FP64 is slow
+// on this chip: evaluated once per grid and step, by the advance kernel and after
+// each upload of the descriptors, never per tile).
+template <typename T>
+__device__ inline void batch_time_factors(BatchGrid<T> *G, double dt) {
+    if (G->vel_kind != VEL_VORTEX) return;
+    const double t = (double)G->step * dt, Tp = G->vp[2];
+    G->vc[0] = (T)cospi(t / Tp);
+    G->vc[1] = (T)cospi((t - dt) / Tp);
+    G->vc[2] = (T)cospi((t + 0.5 * dt) / Tp);
+}
 
 // Parameters common to every grid of a batch (same W, M, cfl, order, flux, precision).
 template <typename T>
@@ -931,13 +852,9 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
         p.qscale = u.qscale;
         p.qinv = u.qinv;
         FastExtra<T> fe;
-        fe.vc_t = fe.vc_told = fe.vc_tface = T(0);
-        if (G->vel_kind == VEL_VORTEX) {
-            const double Tp = G->vp[2];
-            fe.vc_t = (T)cospi(t / Tp);
-            fe.vc_told = (T)cospi((t - u.dt) / Tp);
-            fe.vc_tface = (T)cospi((t + 0.5 * u.dt) / Tp);
-        }
+        fe.vc_t = G->vc[0];
+        fe.vc_told = G->vc[1];
+        fe.vc_tface = G->vc[2];
         const int cur = (int)(step & 1);
         p.X = G->X[cur];
         p.out1 = G->X[1 - cur];
@@ -972,7 +889,7 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
 // and the step counter. One CTA per grid.
 template <typename T>
 __global__ void __launch_bounds__(256)
-batch_advance_kernel(BatchGrid<T> *grids, const double *partials, double *mass, int *status) {
+batch_advance_kernel(BatchGrid<T> *grids, const double *partials, double *mass, int *status, double dt) {
     __shared__ double sred[32];
     BatchGrid<T> *G = grids + blockIdx.x;
     if (G->step >= G->target) return;   // uniform for the CTA
@@ -983,7 +900,15 @@ batch_advance_kernel(BatchGrid<T> *grids, const double *partials, double *mass, 
         mass[blockIdx.x] = s;
         if (!isfinite(s)) atomicOr(status, 1);
         G->step = G->step + 1;
+        batch_time_factors(G, dt);
     }
+}
+
+// The factors of every grid after an upload of the descriptors (one thread per grid).
+template <typename T>
+__global__ void __launch_bounds__(128) batch_factors_kernel(BatchGrid<T> *grids, int n, double dt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) batch_time_factors(grids + i, dt);
 }
 
 }  // namespace dugks

@@ -97,7 +97,9 @@ inline FaceCoefs<T, R> make_face_coefs_r(int order, int flux, double h) {
         };
         if (order == 5) {
             // DUGKS-T2S5: the degree-4 tensor-product Lagrange interpolant on the 5 x 5
-            // cells centred at the cell nearest to x_b - xi h (ties averaged); R = 2
+            // cells centred at the cell nearest to x_b - xi h (ties averaged); it needs
+            // R = 2 (a radius-1 table is never built for order 5)
+            if constexpr (R >= 2) {
             auto L5 = [](int a, double sd) {
                 double w = 1.0;
                 for (int b = -2; b <= 2; b++)
@@ -118,6 +120,7 @@ inline FaceCoefs<T, R> make_face_coefs_r(int order, int flux, double h) {
             if (ky > 0) lagN(0, 1.0, -kx * h, 0.5 - h);
             else if (ky < 0) lagN(1, 1.0, -kx * h, h - 0.5);
             else { lagN(0, 0.5, -kx * h, 0.5); lagN(1, 0.5, -kx * h, -0.5); }
+            }
         } else if (flux == DUGKS_UPWIND) {
             if (kx > 0) addE(0, 1.0, 0.5 - h, -ky * h);
             else if (kx < 0) addE(1, 1.0, h - 0.5, -ky * h);
@@ -195,18 +198,33 @@ inline bool encode_plane_map(CUtensorMap *m, void *base, size_t es, bool half, i
 
 // host doubles (ny * nx, x fastest) -> device plane (double or float) with the
 // periodic ghost border; synchronous
+// A ny * nx field written into a ghost-bordered plane of (ny + 2 GHOST) rows of
+// `pitch` elements of type O: the border holds the periodic images, the padding
+// past nx + 2 GHOST is zero.
+template <typename O>
+inline void fill_ghosted_plane(O *pad, const double *src, int nx, int ny, int pitch) {
+    const int G = GHOST;
+    for (int y = -G; y < ny + G; y++) {
+        const int sy = ((y % ny) + ny) % ny;
+        const double *row = src + (size_t)sy * nx;
+        O *out = pad + (size_t)(y + G) * pitch;
+        for (int x = -G; x < 0; x++) out[x + G] = (O)row[((x % nx) + nx) % nx];
+        for (int x = 0; x < nx; x++) out[x + G] = (O)row[x];
+        for (int x = nx; x < nx + G; x++) out[x + G] = (O)row[x % nx];
+        for (int x = nx + 2 * G; x < pitch; x++) out[x] = O(0);
+    }
+}
+
 inline cudaError_t upload_ghosted_plane(void *dst, const double *src, int nx, int ny, int pitch, bool fp64) {
-    const int G = GHOST, rows = ny + 2 * G;
-    std::vector<double> pad((size_t)rows * pitch, 0.0);
-    for (int y = -G; y < ny + G; y++)
-        for (int x = -G; x < nx + G; x++) {
-            const int sx = ((x % nx) + nx) % nx, sy = ((y % ny) + ny) % ny;
-            pad[(size_t)(y + G) * pitch + (x + G)] = src[(size_t)sy * nx + sx];
-        }
-    if (fp64) return cudaMemcpy(dst, pad.data(), pad.size() * sizeof(double), cudaMemcpyHostToDevice);
-    std::vector<float> f(pad.size());
-    for (size_t i = 0; i < f.size(); i++) f[i] = (float)pad[i];
-    return cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    const size_t n = (size_t)(ny + 2 * GHOST) * pitch;
+    if (fp64) {
+        std::vector<double> pad(n);
+        fill_ghosted_plane(pad.data(), src, nx, ny, pitch);
+        return cudaMemcpy(dst, pad.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    std::vector<float> f(n);
+    fill_ghosted_plane(f.data(), src, nx, ny, pitch);
+    return cudaMemcpy(dst, f.data(), n * sizeof(float), cudaMemcpyHostToDevice);
 }
 
 }  // namespace host

@@ -59,7 +59,9 @@ struct Launch {
 
 template <typename T>
 cudaError_t launch_batch_advance(BatchGrid<T> *grids, int ngrids, const double *partials, double *mass, int *status,
-                                 cudaStream_t s);
+                                 double dt, cudaStream_t s);
+template <typename T>
+cudaError_t launch_batch_factors(BatchGrid<T> *grids, int ngrids, double dt, cudaStream_t s);
 
 cudaError_t launch_mass_final(const double *partial, int n, double *out, int *status, cudaStream_t s);
 
@@ -74,6 +76,9 @@ cudaError_t launch_dvm(const StepParams<T> &p, const DvmExtra<T> &dv, int order,
 // behind a host-side test hook (dugks_selftest_fail_allocs) that can make chosen
 // allocations report cudaErrorMemoryAllocation without touching the device.
 cudaError_t dev_malloc_raw(void **p, size_t bytes);
+// The same hook in front of a stream-ordered allocation from `pool` on stream `s`
+// (cudaMallocFromPoolAsync): the memory is usable in the order of `s`.
+cudaError_t dev_malloc_pool(void **p, size_t bytes, cudaMemPool_t pool, cudaStream_t s);
 template <typename P>
 inline cudaError_t dev_malloc(P **p, size_t bytes) {
     return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);

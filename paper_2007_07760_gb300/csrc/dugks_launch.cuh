@@ -327,9 +327,16 @@ int Launch<T, ST>::batch_ctas_per_sm(int order, int flux, int variant) {
 
 template <typename T>
 cudaError_t launch_batch_advance(BatchGrid<T> *grids, int ngrids, const double *partials, double *mass, int *status,
-                                 cudaStream_t s) {
+                                 double dt, cudaStream_t s) {
     if (ngrids <= 0) return cudaSuccess;
-    batch_advance_kernel<T><<<ngrids, 256, 0, s>>>(grids, partials, mass, status);
+    batch_advance_kernel<T><<<ngrids, 256, 0, s>>>(grids, partials, mass, status, dt);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_batch_factors(BatchGrid<T> *grids, int ngrids, double dt, cudaStream_t s) {
+    if (ngrids <= 0) return cudaSuccess;
+    batch_factors_kernel<T><<<(ngrids + 127) / 128, 128, 0, s>>>(grids, ngrids, dt);
     return cudaGetLastError();
 }
 

@@ -13,8 +13,9 @@ import numpy as np
 
 from . import _build
 
-DUGKS_OK, DUGKS_EINVAL, DUGKS_ENOMEM, DUGKS_ECUDA, DUGKS_ETIMEOUT, DUGKS_ENONFINITE, DUGKS_ESTATE = range(7)
-STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "ESTATE"}
+DUGKS_OK, DUGKS_EINVAL, DUGKS_ENOMEM, DUGKS_ECUDA, DUGKS_ETIMEOUT, DUGKS_ENONFINITE, DUGKS_ESTATE, DUGKS_EAGAIN = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENONFINITE", 6: "ESTATE",
+                7: "EAGAIN"}
 DUGKS_FP64, DUGKS_FP32, DUGKS_FP16F = 0, 1, 2
 DUGKS_UPWIND, DUGKS_CENTRAL = 0, 1
 DUGKS_VEL_UNIFORM, DUGKS_VEL_ROTATION, DUGKS_VEL_VORTEX, DUGKS_VEL_FIELD, DUGKS_VEL_DEFORM = 0, 1, 2, 3, 4
@@ -69,6 +70,11 @@ SIGNATURES = [
     ("dugks_batch_add", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.c_int32, _DP, ctypes.c_int, _DP, _I64,
                                        ctypes.POINTER(ctypes.c_int32)]),
     ("dugks_batch_remove", ctypes.c_int, [_VP, ctypes.c_int32]),
+    ("dugks_batch_retire", ctypes.c_int, [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint64)]),
+    ("dugks_batch_collect", ctypes.c_int, [_VP, ctypes.c_int32, _DP, ctypes.c_int]),
+    ("dugks_batch_fence", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64)]),
+    ("dugks_batch_reached", ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32)]),
+    ("dugks_batch_set_ctas", ctypes.c_int, [_VP, ctypes.c_int32]),
     ("dugks_batch_step", ctypes.c_int, [_VP, _I64]),
     ("dugks_batch_step_index", _I64, [_VP, ctypes.c_int32]),
     ("dugks_batch_read_phi", ctypes.c_int, [_VP, ctypes.c_int32, _DP]),
@@ -272,6 +278,37 @@ def dugks_batch_remove(b, gid: int):
     _bcheck(b, lib().dugks_batch_remove(b, int(gid)))
 
 
+def dugks_batch_retire(b, gid: int) -> int:
+    t = ctypes.c_uint64()
+    _bcheck(b, lib().dugks_batch_retire(b, int(gid), ctypes.byref(t)))
+    return t.value
+
+
+def dugks_batch_collect(b, gid: int, out: np.ndarray, wait: bool = False) -> bool:
+    """True with phi in `out` (freed grid); False if the read-out is still in flight."""
+    r = lib().dugks_batch_collect(b, int(gid), _dptr(out), 1 if wait else 0)
+    if r == DUGKS_EAGAIN:
+        return False
+    _bcheck(b, r)
+    return True
+
+
+def dugks_batch_fence(b) -> int:
+    t = ctypes.c_uint64()
+    _bcheck(b, lib().dugks_batch_fence(b, ctypes.byref(t)))
+    return t.value
+
+
+def dugks_batch_reached(b, ticket: int) -> bool:
+    done = ctypes.c_int32()
+    _bcheck(b, lib().dugks_batch_reached(b, ctypes.c_uint64(int(ticket)), ctypes.byref(done)))
+    return bool(done.value)
+
+
+def dugks_batch_set_ctas(b, ctas: int):
+    _bcheck(b, lib().dugks_batch_set_ctas(b, int(ctas)))
+
+
 def dugks_batch_step(b, nsteps: int):
     _bcheck(b, lib().dugks_batch_step(b, int(nsteps)))
 
@@ -342,6 +379,27 @@ class Batch:
 
     def step_index(self, gid: int) -> int:
         return dugks_batch_step_index(self.b, gid)
+
+    def retire(self, gid: int) -> int:
+        """Freezes the grid and queues its read-out; returns the fence ticket."""
+        return dugks_batch_retire(self.b, gid)
+
+    def collect(self, gid: int, wait: bool = False):
+        """phi of a retired grid (the grid is freed), or None while the copy is in flight."""
+        out = np.empty(self.shapes[gid])
+        if not dugks_batch_collect(self.b, gid, out, wait):
+            return None
+        self.shapes.pop(gid, None)
+        return out
+
+    def fence(self) -> int:
+        return dugks_batch_fence(self.b)
+
+    def reached(self, ticket: int) -> bool:
+        return dugks_batch_reached(self.b, ticket)
+
+    def set_ctas(self, ctas: int):
+        dugks_batch_set_ctas(self.b, ctas)
 
     def phi(self, gid: int) -> np.ndarray:
         out = np.empty(self.shapes[gid])
