@@ -124,22 +124,6 @@ __device__ __forceinline__ int wrap_small(int i, int n) {
     return i;
 }
 
-// periodic images of one value inside the ghost border (cells near an edge only)
-template <typename T, typename V>
-__device__ __noinline__ void put_ghosts(const StepParams<T> &p, V *plane, int x, int y, V v) {
-#pragma unroll 1
-    for (int ay = -1; ay <= 1; ay++) {
-        const int yy = y + ay * p.ny;
-        if (yy < -GHOST || yy >= p.ny + GHOST) continue;
-#pragma unroll 1
-        for (int ax = -1; ax <= 1; ax++) {
-            const int xx = x + ax * p.nx;
-            if ((ax == 0 && ay == 0) || xx < -GHOST || xx >= p.nx + GHOST) continue;
-            plane[gidx(p, xx, yy)] = v;
-        }
-    }
-}
-
 // four consecutive shared-memory values (16-B aligned for float, two 16-B loads for double)
 __device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
     const float4 q = *reinterpret_cast<const float4 *>(p);
@@ -150,20 +134,28 @@ __device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
     v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
 
+// Plane geometry for the ghost writer: passed by value, so that a caller whose
+// parameters are a local struct (the many-grid kernel) does not have to keep that
+// struct in local memory for the call.
+struct GhostGeom {
+    int nx, ny, pitch;
+    size_t plane;
+};
+
 // ghost images of the 9 distribution values and phi of one cell near an edge
 // (values by argument so that the caller's registers stay registers)
 template <typename T, typename V>
-__device__ __noinline__ void put_ghosts9(const StepParams<T> &p, V *out, int x, int y, T phi, V v0, V v1, V v2,
+__device__ __noinline__ void put_ghosts9(GhostGeom gg, T *phi_out, V *out, int x, int y, T phi, V v0, V v1, V v2,
                                          V v3, V v4, V v5, V v6, V v7, V v8) {
 #pragma unroll 1
     for (int ay = -1; ay <= 1; ay++) {
-        const int yy = y + ay * p.ny;
-        if (yy < -GHOST || yy >= p.ny + GHOST) continue;
+        const int yy = y + ay * gg.ny;
+        if (yy < -GHOST || yy >= gg.ny + GHOST) continue;
 #pragma unroll 1
         for (int ax = -1; ax <= 1; ax++) {
-            const int xx = x + ax * p.nx;
-            if ((ax == 0 && ay == 0) || xx < -GHOST || xx >= p.nx + GHOST) continue;
-            const size_t g = gidx(p, xx, yy), pl = p.plane;
+            const int xx = x + ax * gg.nx;
+            if ((ax == 0 && ay == 0) || xx < -GHOST || xx >= gg.nx + GHOST) continue;
+            const size_t g = (size_t)(yy + GHOST) * gg.pitch + (size_t)(xx + GHOST), pl = gg.plane;
             out[g] = v0;
             out[pl + g] = v1;
             out[2 * pl + g] = v2;
@@ -173,7 +165,7 @@ __device__ __noinline__ void put_ghosts9(const StepParams<T> &p, V *out, int x, 
             out[6 * pl + g] = v6;
             out[7 * pl + g] = v7;
             out[8 * pl + g] = v8;
-            if (p.phi_out != nullptr) p.phi_out[g] = phi;
+            if (phi_out != nullptr) phi_out[g] = phi;
         }
     }
 }
@@ -270,6 +262,7 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = p.nx, ny = p.ny;
+    const GhostGeom gg{nx, ny, p.pitch, p.plane};
     const int x0 = bx * TX, y0 = by * TY;
     // padded-plane coordinates of the state box; ox = offset of relative x = -H in the box
     const int xs_raw = x0 - H + GHOST, ys = y0 - H + GHOST;
@@ -645,7 +638,8 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
 #pragma unroll
                 for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
                 p.phi_out[g] = pho;
-                if (edge) put_ghosts9(p, O, gx, gy, pho, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
+                if (edge) put_ghosts9(gg, p.phi_out, O, gx, gy, pho,
+                                      o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
                 T o2[9];
                 const T ph2 = combine(p.ga2, gmc2, cg[r], [&](int k) { return part2_ref(k, r); }, o2, mix32(bits));
 #pragma unroll
@@ -664,7 +658,8 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
 #pragma unroll
                 for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
                 if constexpr (PHIP) p.phi_out[g] = phn;   // phi^{n+1} (else phi_out is null)
-                if (edge) put_ghosts9(p, O, gx, gy, phn, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
+                if (edge) put_ghosts9(gg, p.phi_out, O, gx, gy, phn,
+                                      o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
                 msum += (double)phn;
             }
             continue;
@@ -707,7 +702,8 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
             }
             p.phi_out[g] = phn;
             if (edge)
-                put_ghosts9(p, Oq, gx, gy, phn, qv[0], qv[1], qv[2], qv[3], qv[4], qv[5], qv[6], qv[7], qv[8]);
+                put_ghosts9(gg, p.phi_out, Oq, gx, gy, phn,
+                            qv[0], qv[1], qv[2], qv[3], qv[4], qv[5], qv[6], qv[7], qv[8]);
         } else {
             // a phi plane receives the new phi; otherwise phi_out is phi of X (the
             // older level of the next step's d(phi u)/dt)
@@ -716,7 +712,8 @@ __device__ __forceinline__ bool fast_tile(const StepParams<T> &p, const FaceCoef
 #pragma unroll
             for (int k = 0; k < 9; k++) O[k * plane + g] = o[k];
             p.phi_out[g] = pho;
-            if (edge) put_ghosts9(p, O, gx, gy, pho, o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
+            if (edge) put_ghosts9(gg, p.phi_out, O, gx, gy, pho,
+                                  o[0], o[1], o[2], o[3], o[4], o[5], o[6], o[7], o[8]);
         }
         msum += (double)phn;
     }
@@ -772,16 +769,21 @@ struct alignas(64) BatchGrid {
     int item0, nitems;       // its tiles in the work list
     int vel_kind, pad_;
     double vp[3];            // velocity parameters (FP64; rounded per precision in the kernel)
-    T vc[3];                 // single vortex: cos(pi t / T) at t, t - dt, t + dt/2 of the current step
+    T tl[3];                 // time levels of the current step: t, t - dt, t + dt/2
+    T vc[3];                 // single vortex: cos(pi t / T) at those levels
 };
 
-// Reversal factors of a vortex grid for its current step, in FP64 (FP64 is slow
-// on this chip: evaluated once per grid and step, by the advance kernel and after
-// each upload of the descriptors, never per tile).
+// Time levels of a grid's current step and, for the single vortex, its reversal
+// factors, in FP64 (FP64 is slow on this chip: evaluated once per grid and step,
+// by the advance kernel and after each upload of the descriptors, never per tile).
 template <typename T>
 __device__ inline void batch_time_factors(BatchGrid<T> *G, double dt) {
+    const double t = (double)G->step * dt;
+    G->tl[0] = (T)t;
+    G->tl[1] = (T)(t - dt);
+    G->tl[2] = (T)(t + 0.5 * dt);
     if (G->vel_kind != VEL_VORTEX) return;
-    const double t = (double)G->step * dt, Tp = G->vp[2];
+    const double Tp = G->vp[2];
     G->vc[0] = (T)cospi(t / Tp);
     G->vc[1] = (T)cospi((t - dt) / Tp);
     G->vc[2] = (T)cospi((t + 0.5 * dt) / Tp);
@@ -806,6 +808,7 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
     uint64_t *bar = fast_bar<T, ST, NW, MR>(smem);
     if (threadIdx.x == 0) mbar_init(bar, 1);
     uint32_t phase = 0;
+    int fenced = -1;   // grid whose tensor maps this CTA has acquired in this launch
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const int4 w = items[it];
         const BatchGrid<T> *G = grids + w.x;
@@ -845,10 +848,9 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
         p.vp0 = (T)G->vp[0];
         p.vp1 = (T)G->vp[1];
         p.vp2 = (T)G->vp[2];
-        const double t = (double)step * u.dt;
-        p.t = (T)t;
-        p.t_old = (T)(t - u.dt);
-        p.t_face = (T)(t + 0.5 * u.dt);
+        p.t = G->tl[0];
+        p.t_old = G->tl[1];
+        p.t_face = G->tl[2];
         p.qscale = u.qscale;
         p.qinv = u.qinv;
         FastExtra<T> fe;
@@ -871,8 +873,10 @@ batch_fast_kernel(const __grid_constant__ BatchUniform<T> u, const __grid_consta
         }
         p.phi_old = G->phi[iPo];
         p.phi_out = G->phi[iOut];
-        if (threadIdx.x == 0) {
-            // tensor maps written to global memory by the host: order them for the TMA unit
+        if (threadIdx.x == 0 && w.x != fenced) {
+            // tensor maps written to global memory by the host: order them for the TMA
+            // unit (once per grid: the descriptors do not change during a launch)
+            fenced = w.x;
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmX[cur]) : "memory");
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&G->tmPhi[iPo]) : "memory");
             if constexpr (PHIP)
