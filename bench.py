@@ -70,6 +70,7 @@ L2_FLUSH_BYTES = 512 << 20
 NCU_TRAFFIC = {
     ("be0cd082f03ff3ee", "vortex1024_fp32_p3_upwind_2stage"): 50321024,     # mean of two launches
     ("be0cd082f03ff3ee", "vortex4096_fp32_p3_upwind_2stage"): 1383682304,   # state 11x the L2
+    ("be0cd082f03ff3ee", "batch512_fp32_p3_upwind_2stage"): 3315071744,     # 1.21x: halos of small grids
 }
 
 

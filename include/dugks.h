@@ -181,7 +181,7 @@ const char *dugks_last_error(const dugks_ctx *c);
 
 /* Tile variant of the TMA-staged two-stage kernel (orders 2, 3), warps per CTA x
  * rows of cells per thread: 0 = 8 x 4 (FP64: 8 x 2), 1 = 16 x 1, 2 = 8 x 2,
- * 3 = 16 x 2, 4 = 8 x 3, 5 = 4 x 4 (a tile is 31 cells wide and warps x rows - 1
+ * 3 = 12 x 3, 4 = 8 x 3, 5 = 10 x 4 (a tile is 31 cells wide and warps x rows - 1
  * cells high). The default is 2 below 512 x 512 cells and 4 from there up; -1
  * selects the generic fused kernel (one thread per cell and stage, no TMA), the
  * plain comparison path. A tuning choice only: results agree to rounding.

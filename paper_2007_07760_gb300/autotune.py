@@ -9,9 +9,10 @@ run is long enough (at least ~2 ms of device work) that the launch and
 synchronisation cost is small, and the best of three repeats is kept. The
 variants run the same per-cell arithmetic (they agree to rounding; the tests
 check it against the oracle and against each other), so the choice is a speed
-one. Temporal blocking is not offered: the step kernel is bound by instruction
-issue, not by HBM, so recomputing halos to save HBM round trips would slow it
-down.
+one. Temporal blocking is not offered, on a measurement: the 1024^2 step with
+its whole state resident in L2 between steps (what fusing steps would give) runs
+only 5% faster than with L2 flushed before every step, while a second fused step
+would recompute a halo of 60% more cells in an issue-bound kernel.
 """
 from __future__ import annotations
 
@@ -48,9 +49,13 @@ def _store(d: dict):
         pass
 
 
+# bumped whenever a variant number changes its tile shape (older cache entries are ignored)
+TABLE = 2
+
+
 def key(kind: str, params, cells: int) -> str:
     bucket = int(round(math.log2(max(cells, 1))))
-    return f"{kind}/p{params.precision}/o{params.order}/f{params.flux}/c2^{bucket}"
+    return f"t{TABLE}/{kind}/p{params.precision}/o{params.order}/f{params.flux}/c2^{bucket}"
 
 
 def _time_steps(step_fn, sync_fn, steps: int) -> float:

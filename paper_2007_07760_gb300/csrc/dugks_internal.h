@@ -17,8 +17,9 @@ constexpr int TILE_Y = 8;
 constexpr int STEP_THREADS = 256;
 
 // Fast-kernel variants (warps per CTA x rows per thread): 0 = 8 x 4 (FP64: 8 x 2),
-// 1 = 16 x 1, 2 = 8 x 2, 3 = 16 x 2, 4 = 8 x 3, 5 = 4 x 4. Fewer rows per thread:
-// fewer registers and more resident warps, more halo overhead.
+// 1 = 16 x 1, 2 = 8 x 2, 3 = 12 x 3, 4 = 8 x 3, 5 = 10 x 4. Fewer rows per thread:
+// fewer registers and more resident warps, more halo overhead; taller tiles (3, 5):
+// less halo per cell, fewer resident CTAs.
 constexpr int FAST_VARIANTS = 6;
 
 // Geometry of a TMA-staged (fast) variant.

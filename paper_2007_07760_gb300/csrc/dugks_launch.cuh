@@ -98,9 +98,9 @@ FastGeom Launch<T, ST>::fast_geom(int variant, int order) {
     switch (variant) {
     case 1: return geom_t<T, ST, 16, 1>();
     case 2: return geom_t<T, ST, 8, 2>();
-    case 3: return geom_t<T, ST, 16, 2>();
+    case 3: return geom_t<T, ST, 12, 3>();
     case 4: return geom_t<T, ST, 8, 3>();
-    case 5: return geom_t<T, ST, 4, 4>();
+    case 5: return geom_t<T, ST, 10, 4>();
     default: return geom_t<T, ST, 8, fast_mr<T>()>();
     }
 }
@@ -133,9 +133,9 @@ static cudaError_t launch_fast_v(const StepParams<T> &p, const FaceCoefs<T> &cf,
     switch (variant) {
     case 1: return launch_fast_t<T, ST, ORDER, FLUX, 16, 1>(p, cf, fe, tmX, tmPo, tmPc, s);
     case 2: return launch_fast_t<T, ST, ORDER, FLUX, 8, 2>(p, cf, fe, tmX, tmPo, tmPc, s);
-    case 3: return launch_fast_t<T, ST, ORDER, FLUX, 16, 2>(p, cf, fe, tmX, tmPo, tmPc, s);
+    case 3: return launch_fast_t<T, ST, ORDER, FLUX, 12, 3>(p, cf, fe, tmX, tmPo, tmPc, s);
     case 4: return launch_fast_t<T, ST, ORDER, FLUX, 8, 3>(p, cf, fe, tmX, tmPo, tmPc, s);
-    case 5: return launch_fast_t<T, ST, ORDER, FLUX, 4, 4>(p, cf, fe, tmX, tmPo, tmPc, s);
+    case 5: return launch_fast_t<T, ST, ORDER, FLUX, 10, 4>(p, cf, fe, tmX, tmPo, tmPc, s);
     default: return launch_fast_t<T, ST, ORDER, FLUX, 8, fast_mr<T>()>(p, cf, fe, tmX, tmPo, tmPc, s);
     }
 }
@@ -279,9 +279,9 @@ static int batch_occupancy_t() {
     switch (variant) {                                                                        \
     case 1: return CALL(16, 1);                                                               \
     case 2: return CALL(8, 2);                                                                \
-    case 3: return CALL(16, 2);                                                               \
+    case 3: return CALL(12, 3);                                                               \
     case 4: return CALL(8, 3);                                                                \
-    case 5: return CALL(4, 4);                                                                \
+    case 5: return CALL(10, 4);                                                               \
     default: return CALL(8, fast_mr<T>());                                                    \
     }
 
