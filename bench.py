@@ -68,9 +68,9 @@ L2_FLUSH_BYTES = 512 << 20
 # writes of a 1024^2 step stay in L2 (129 MB) during the launch and reach DRAM
 # later, so the figure is the read traffic plus the evictions.
 NCU_TRAFFIC = {
-    ("be0cd082f03ff3ee", "vortex1024_fp32_p3_upwind_2stage"): 50321024,     # mean of two launches
-    ("be0cd082f03ff3ee", "vortex4096_fp32_p3_upwind_2stage"): 1383682304,   # state 11x the L2
-    ("be0cd082f03ff3ee", "batch512_fp32_p3_upwind_2stage"): 3315071744,     # 1.21x: halos of small grids
+    ("39695d0b35e04f01", "vortex1024_fp32_p3_upwind_2stage"): 50221952,     # mean of two launches
+    ("39695d0b35e04f01", "vortex4096_fp32_p3_upwind_2stage"): 1383376128,   # state 11x the L2
+    ("39695d0b35e04f01", "batch512_fp32_p3_upwind_2stage"): 3282068992,     # 1.20x: halos of small grids
 }
 
 

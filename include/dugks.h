@@ -186,7 +186,8 @@ const char *dugks_last_error(const dugks_ctx *c);
  * selects the generic fused kernel (one thread per cell and stage, no TMA), the
  * plain comparison path. A tuning choice only: results agree to rounding.
  * Returns DUGKS_EINVAL for any other number. Order 4 and the three-stage
- * scheme have one TMA-staged tile shape each (8 x 2): any variant >= 0 selects it.
+ * scheme have one TMA-staged tile shape each (orders 4-5, two-stage: 10 x 3, FP64
+ * 8 x 2; three-stage: 8 x 2): any variant >= 0 selects it.
  * dugks_get_variant returns -1 when the context uses the generic kernel. */
 int dugks_set_variant(dugks_ctx *c, int variant);
 int dugks_get_variant(const dugks_ctx *c);

@@ -143,7 +143,7 @@ bool encode_map(CUtensorMap *m, void *base, size_t es, bool half, const dugks_ct
 
 template <typename T, typename ST>
 bool setup_fast(dugks_ctx *c) {
-    const FastGeom g = Launch<T, ST>::fast_geom(c->variant, c->p.order);
+    const FastGeom g = Launch<T, ST>::fast_geom(c->variant, c->p.order, c->p.stages);
     const bool half = Store<T, ST>::deviation;
     for (int s = 0; s < 2; s++)
         if (!encode_map(&c->tmX[s], c->X[s], sizeof(ST), half, c, 9, g.box_w, g.box_h)) return false;
@@ -617,7 +617,7 @@ int dugks_create(const dugks_params *p, const double *phi0_host, void *cuda_stre
     // (three-stage); FP64: the previous level for d(phi u)/dt (and phi^n, three-stage)
     c->nphi = p->precision == DUGKS_FP64 ? 2 : p->stages == 3 ? 4 : 3;
     // the TMA-staged kernels serve every order and both schemes (three-stage: full
-    // storage; order 4 and the three-stage scheme: one tile shape, 8 x 2)
+    // storage; orders 4-5 and the three-stage scheme: one tile shape each)
     // (the DVM has one kernel of its own)
     c->fast = p->stages != 1 && (p->stages == 2 || p->precision != DUGKS_FP16F) && encode_fn() != nullptr;
     if (c->fast && (p->stages == 3 || p->order >= 4)) {

@@ -3,6 +3,6 @@
 #include "dugks_launch.cuh"
 
 namespace dugks {
-template FastGeom Launch<float,float>::fast_geom(int, int);
+template FastGeom Launch<float,float>::fast_geom(int, int, int);
 template cudaError_t Launch<float,float>::step_fast(const StepParams<float> &, const FaceCoefs<float> &, const FastExtra<float> &, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, int, int, int, cudaStream_t);
 }  // namespace dugks

@@ -3,6 +3,6 @@
 #include "dugks_launch.cuh"
 
 namespace dugks {
-template FastGeom Launch<double,double>::fast_geom(int, int);
+template FastGeom Launch<double,double>::fast_geom(int, int, int);
 template cudaError_t Launch<double,double>::step_fast(const StepParams<double> &, const FaceCoefs<double> &, const FastExtra<double> &, const CUtensorMap &, const CUtensorMap &, const CUtensorMap &, int, int, int, cudaStream_t);
 }  // namespace dugks

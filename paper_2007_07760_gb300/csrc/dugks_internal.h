@@ -37,7 +37,7 @@ struct Launch {
     static cudaError_t phi(const StepParams<T> &p, T *out, cudaStream_t s);
     // phi widened to double on the device (host read-out: one copy, no host conversion)
     static cudaError_t phi64(const StepParams<T> &p, double *out, cudaStream_t s);
-    static FastGeom fast_geom(int variant, int order = 3);
+    static FastGeom fast_geom(int variant, int order = 3, int stages = 2);
     static cudaError_t batch_step(const BatchUniform<T> &u, const FaceCoefs<T> &cf, const BatchGrid<T> *grids,
                                   const int4 *items, int nitems, double *partials, int order, int flux, int variant,
                                   int ctas, cudaStream_t s);
