@@ -292,7 +292,8 @@ int dugks_batch_read_phi(dugks_batch *b, int32_t grid_id, double *out_host);
 /* Waits and returns one grid's mass (FP64, fixed-order sum). */
 int dugks_batch_mass(dugks_batch *b, int32_t grid_id, double *out);
 
-/* Tile variant of the batch kernel (0..5 as for dugks_set_variant; default 4);
+/* Tile variant of the batch kernel (0..5 as for dugks_set_variant; default 5 in
+ * FP32, 4 otherwise);
  * waits for the stream and rebuilds the grid descriptors. */
 int dugks_batch_set_variant(dugks_batch *b, int variant);
 

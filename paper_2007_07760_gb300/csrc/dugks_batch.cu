@@ -61,7 +61,7 @@ struct dugks_batch {
     bool own_stream = false;
     size_t tsize = 4, ssize = 4;
     int nphi = 2;
-    // 8 warps x 3 rows per thread measured fastest on mixed batches (FP32)
+    // 8 warps x 3 rows per thread; FP32: 10 x 4 (measured fastest on mixed batches)
     int variant = 4;
     int ctas = 0;
     int ctas_req = 0;   // 0: resident CTAs (grid-stride); < 0: one CTA per tile; > 0: at most that many
@@ -579,6 +579,7 @@ int dugks_batch_create(const dugks_params *common, void *cuda_stream, dugks_batc
     b->tsize = fp64(b) ? 8 : 4;
     b->ssize = common->precision == DUGKS_FP64 ? 8 : common->precision == DUGKS_FP32 ? 4 : 2;
     b->nphi = common->precision == DUGKS_FP64 ? 2 : 3;   // FP32 and FP16F: phi is a plane of its own
+    if (common->precision == DUGKS_FP32) b->variant = 5;
     if (const char *ev = std::getenv("DUGKS_FAST_VARIANT")) {
         const int v = std::atoi(ev);
         if (v >= 0 && v < FAST_VARIANTS) b->variant = v;
