@@ -356,6 +356,7 @@ class Batch:
         self.params = make_params(8, 8, **kw)
         self.b = dugks_batch_create(self.params, stream)
         self.shapes = {}
+        self.tickets = {}   # grid id -> fence ticket of its pending read-out
 
     def grid_bytes(self, nx: int, ny: int) -> int:
         return dugks_batch_grid_bytes(self.params, nx, ny)
@@ -372,6 +373,7 @@ class Batch:
     def remove(self, gid: int):
         dugks_batch_remove(self.b, gid)
         self.shapes.pop(gid, None)
+        self.tickets.pop(gid, None)
 
     def step(self, n: int = 1):
         dugks_batch_step(self.b, n)
@@ -382,14 +384,20 @@ class Batch:
 
     def retire(self, gid: int) -> int:
         """Freezes the grid and queues its read-out; returns the fence ticket."""
-        return dugks_batch_retire(self.b, gid)
+        t = dugks_batch_retire(self.b, gid)
+        self.tickets[gid] = t
+        return t
 
     def collect(self, gid: int, wait: bool = False):
         """phi of a retired grid (the grid is freed), or None while the copy is in flight."""
+        t = self.tickets.get(gid)
+        if not wait and t is not None and not dugks_batch_reached(self.b, t):
+            return None   # (no output buffer made while the copy is in flight)
         out = np.empty(self.shapes[gid])
         if not dugks_batch_collect(self.b, gid, out, wait):
             return None
         self.shapes.pop(gid, None)
+        self.tickets.pop(gid, None)
         return out
 
     def fence(self) -> int:

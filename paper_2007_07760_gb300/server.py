@@ -152,7 +152,6 @@ class Server:
             else:
                 self.lanes.append(Lane(ln, None, slice_steps))
         self.lanes[-1].max_work = None
-        self.b = self.lanes[0].backend
         self.budget = budget_bytes
         self.max_slots = max_slots
         self.keep = keep_fields
