@@ -106,11 +106,11 @@ def request_field(req: Request, cfl: float = 0.8, W: float = 4.0, umax: float = 
         s = n / 256.0
         if phi0 is None:
             phi0 = WL.slotted_disk(n, 128 * s, 160 * s, 64 * s, 16 * s, 80 * s, W)
-        omega = min(2.0 * math.pi / (req.steps * cfl), umax * math.sqrt(2.0) / n)
+        omega = min(2.0 * math.pi / (max(req.steps, 1) * cfl), umax * math.sqrt(2.0) / n)
         return phi0, "rotation", (n / 2, n / 2, omega)
     if phi0 is None:
         phi0 = WL.drops(n, n, [(0.5 * n, 0.75 * n)], [0.15 * n], W)
-    return phi0, "vortex", (float(n), umax, req.steps * cfl)
+    return phi0, "vortex", (float(n), umax, max(req.steps, 1) * cfl)   # (a zero-step request: T of one step)
 
 
 @dataclass

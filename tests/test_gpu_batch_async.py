@@ -145,3 +145,19 @@ def test_async_call_errors():
         b.retire(g3)
         assert np.array_equal(b.collect(g3, wait=True), _solo(a, "uniform", (0.01, 0.0), 3))
         assert b.status() == 0
+
+
+def test_edge_cases_empty_batch_and_retire_before_any_step():
+    (a,) = _fields(5, [(40, 56)])
+    with N.Batch(**COMMON) as b:
+        b.step(10)                      # no grids: nothing to do, no error
+        t = b.fence()
+        assert b.status() == 0 and b.reached(t)
+        g = b.add(a, "vortex", (56.0, 0.05, 100.0), 30)
+        b.retire(g)                     # at step 0: the initial field's phi
+        got = _collect(b, g)
+        b.step(5)                       # the batch is empty again
+        assert b.status() == 0
+    with N.Batch(**COMMON) as ref:
+        r = ref.add(a, "vortex", (56.0, 0.05, 100.0), 30)
+        assert np.array_equal(got, ref.phi(r))

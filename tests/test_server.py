@@ -328,6 +328,20 @@ def test_out_of_memory_beside_resident_grids_fails_and_ends():
     assert clock.t < 1e3
 
 
+def test_zero_step_request_is_served():
+    clock = FakeClock()
+    fb = FakeBatch(clock)
+    srv = S.Server(fb, budget_bytes=1 << 30, slice_steps=16, clock=clock, sleep=clock.sleep)
+    reqs = [S.Request(0, 0.0, 64, 0, "vortex"), S.Request(1, 0.0, 48, 0, "rotation"),
+            S.Request(2, 0.0, 32, 40, "rotation")]
+    for r in reqs:   # the velocity of a zero-step request is still a valid one
+        phi0, kind, vel = S.request_field(r)
+        assert np.isfinite(vel).all() and (kind != "vortex" or vel[2] > 0)
+    st = srv.run(reqs)
+    assert st["requests"] == 3 and st["failed"] == 0
+    assert srv.cell_updates == 32 * 32 * 40
+
+
 @pytest.mark.gpu
 def test_served_non_finite_request_fails_alone():
     from paper_2007_07760_gb300 import native as N
@@ -380,6 +394,7 @@ def test_served_in_priority_lanes_equal_solo_runs():
     from paper_2007_07760_gb300 import native as N
     common = dict(W=4.0, M=0.02, cfl=0.8, order=3, flux=0, stages=2, precision="fp32")
     trace = S.poisson_trace(24, rate=3000.0, seed=11, nmin=32, nmax=128, smin=20, smax=160)
+    trace.append(S.Request(24, 0.001, 48, 0, "rotation"))   # zero steps: the initial field comes back
     streams = [torch.cuda.Stream(priority=p) for p in (-2, -1, 0)]
     batches = [N.Batch(stream=s.cuda_stream, **common) for s in streams]
     try:
